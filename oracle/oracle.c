@@ -1,0 +1,480 @@
+/*
+ * oracle.c -- FP64 CPU oracle for the road-surface stereo hot path of
+ * Fan et al., "Real-Time Stereo Vision for Road Surface 3-D Reconstruction"
+ * (arXiv 1807.07433).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline / reference arm may load this
+ * library.  The CUDA path shares no code, header, table or helper with it.
+ *
+ * Every quantity is computed by its direct definition in double precision:
+ * explicit window sums (no running sums, no integral images), explicit
+ * neighbourhood sums for the bilateral filter, a linear scan for the argmax.
+ * Where the paper is silent the reading used is stated at the function.
+ *
+ * Layouts: images are row-major [H][W] (index v*W+u); cost volumes and
+ * aggregated volumes are [H][W][D] (index (v*W+u)*D+d); XYZ is three planes
+ * [3][H][W].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int W, H;          /* image size */
+    int D;             /* number of residual disparities searched: 0..D-1 */
+    int ncc_r;         /* NCC block radius (rho-script in Eq. 3); n = (2r+1)^2 */
+    int agg_r;         /* bilateral window radius (rho in Eq. 8) */
+    double gamma_d;    /* Eq. 9 */
+    double gamma_r;    /* Eq. 10 */
+    double lr_thresh;  /* L-R consistency tolerance in pixels (Eq. 11 is 0) */
+    double alpha0, alpha1, delta; /* Eq. 2 plane and the offset of Sec. II-A */
+    double f_px, baseline, u0, v0; /* camera for Sec. II-D */
+} orc_params;
+
+/* Optional outputs; any pointer may be NULL.  Arrays are full-frame sized
+ * even when only a band of rows is computed (rows outside are untouched). */
+typedef struct {
+    double *warped;           /* [H][W] i_r' after the perspective transform */
+    double *mu_l, *sig_l;     /* [H][W] block mean / std of i_l  (Eq. 4) */
+    double *mu_r, *sig_r;     /* [H][W] block mean / std of i_r' (Eq. 5) */
+    double *cost_l, *cost_r;  /* [H][W][D] raw NCC volumes (Eq. 3) */
+    double *agg_l, *agg_r;    /* [H][W][D] aggregated volumes (Eq. 8) */
+    int32_t *lbl_l, *lbl_r;   /* [H][W] WTA maps l_ref, l_tar */
+    double *gap_l, *gap_r;    /* [H][W] best minus second-best aggregated cost */
+    double *den_l;            /* [H][W] parabola denominator of Eq. 12 (0 at ends) */
+    double *dsub;             /* [H][W] subpixel residual disparity d^s */
+    uint8_t *valid;           /* [H][W] 1 where the L-R check passes */
+    double *dfull;            /* [H][W] post-processed disparity, NaN if rejected */
+    double *xyz;              /* [3][H][W] reconstructed points, NaN if rejected */
+} orc_outputs;
+
+static int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* Sec. II-A: every point of target row v is shifted alpha0 + alpha1*v - delta
+ * pixels to the right (Eq. 2 gives the road-plane disparity alpha0+alpha1*v). */
+double orc_row_shift(const orc_params *p, int v) {
+    return p->alpha0 + p->alpha1 * (double)v - p->delta;
+}
+
+/* Sec. II-A perspective transformation of the target image.
+ * Reading: a shift by s to the right means i_r'(x,v) = i_r(x - s, v); a
+ * non-integer shift is linear interpolation along x (what bilinear resampling
+ * reduces to for a pure row shift); source columns outside the image are
+ * clamped to the edge.  With k = floor(s), w = s - k:
+ *     i_r'(x,v) = (1-w) i_r(x-k, v) + w i_r(x-k-1, v). */
+void orc_warp(const orc_params *p, const uint8_t *ir, double *out) {
+    const int W = p->W, H = p->H;
+    for (int v = 0; v < H; ++v) {
+        const double s = orc_row_shift(p, v);
+        const double k = floor(s);
+        const double w = s - k;
+        const int ki = (int)k;
+        for (int x = 0; x < W; ++x) {
+            const double a = ir[(size_t)v * W + clampi(x - ki, 0, W - 1)];
+            const double b = ir[(size_t)v * W + clampi(x - ki - 1, 0, W - 1)];
+            out[(size_t)v * W + x] = (1.0 - w) * a + w * b;
+        }
+    }
+}
+
+/* Eqs. 4-5: mean and population standard deviation of the (2r+1)x(2r+1)
+ * block centred at (u,v).  Reading: pixels outside the image are read
+ * clamp-to-edge, so a block is defined for any integer centre.
+ * Returns the variance; writes mu and sigma. */
+double orc_block_stats(const double *img, int W, int H, int r, int u, int v,
+                       double *mu, double *sigma) {
+    const double n = (double)((2 * r + 1) * (2 * r + 1));
+    double s = 0.0, s2 = 0.0;
+    for (int j = -r; j <= r; ++j) {
+        const int y = clampi(v + j, 0, H - 1);
+        for (int i = -r; i <= r; ++i) {
+            const double val = img[(size_t)y * W + clampi(u + i, 0, W - 1)];
+            s += val;
+            s2 += val * val;
+        }
+    }
+    const double m = s / n;
+    double var = s2 / n - m * m;          /* Eq. 4 / Eq. 5 under the root */
+    if (var < 0.0) var = 0.0;
+    if (mu) *mu = m;
+    if (sigma) *sigma = sqrt(var);
+    return var;
+}
+
+/* Variance below which a block is treated as flat and its NCC is 0
+ * (reading: Eq. 3 divides by n*sigma_l*sigma_r, undefined for a flat block). */
+#define ORC_FLAT_VAR 1e-6
+
+/* Eq. 3: normalised cross-correlation between the left block centred at
+ * (ul, v) and the right block centred at (ur, v) of the warped target.
+ * In the paper's notation ul = u and ur = u - d. */
+double orc_ncc(const double *L, const double *R, int W, int H, int r,
+               int ul, int ur, int v) {
+    double mu_l, sig_l, mu_r, sig_r;
+    const double var_l = orc_block_stats(L, W, H, r, ul, v, &mu_l, &sig_l);
+    const double var_r = orc_block_stats(R, W, H, r, ur, v, &mu_r, &sig_r);
+    if (var_l < ORC_FLAT_VAR || var_r < ORC_FLAT_VAR) return 0.0;
+    const double n = (double)((2 * r + 1) * (2 * r + 1));
+    double dot = 0.0;
+    for (int j = -r; j <= r; ++j) {
+        const int y = clampi(v + j, 0, H - 1);
+        for (int i = -r; i <= r; ++i) {
+            dot += L[(size_t)y * W + clampi(ul + i, 0, W - 1)] *
+                   R[(size_t)y * W + clampi(ur + i, 0, W - 1)];
+        }
+    }
+    return (dot - n * mu_l * mu_r) / (n * sig_l * sig_r);
+}
+
+/* Eqs. 8-10: bilateral aggregation of cost slice d at (u,v).
+ * vol is [H][W][D]; g is the guide image whose intensities drive omega_r.
+ * Readings: Eqs. 9-10 carry no factor 2; neighbours outside the image are
+ * left out of both sums. */
+double orc_bilateral(const double *vol, int D, int d, const double *g, int W, int H,
+                     int rho, double gamma_d, double gamma_r, int u, int v) {
+    const double gc = g[(size_t)v * W + u];
+    double num = 0.0, den = 0.0;
+    for (int dy = -rho; dy <= rho; ++dy) {
+        const int y = v + dy;
+        if (y < 0 || y >= H) continue;
+        for (int dx = -rho; dx <= rho; ++dx) {
+            const int x = u + dx;
+            if (x < 0 || x >= W) continue;
+            const double wd = exp(-(double)(dx * dx + dy * dy) / (gamma_d * gamma_d)); /* Eq. 9 */
+            const double di = g[(size_t)y * W + x] - gc;
+            const double wr = exp(-(di * di) / (gamma_r * gamma_r));                  /* Eq. 10 */
+            num += wd * wr * vol[((size_t)y * W + x) * D + d];
+            den += wd * wr;
+        }
+    }
+    return num / den;
+}
+
+/* Bilateral aggregation of every disparity at (u,v): out[d] for d in [0,D).
+ * Each out[d] is exactly the sum of orc_bilateral (same terms, same order);
+ * the weights are simply evaluated once per neighbour. */
+static void bilateral_all_d(const double *vol, int D, const double *g, int W, int H,
+                            int rho, double gamma_d, double gamma_r, int u, int v,
+                            double *num, double *out) {
+    const double gc = g[(size_t)v * W + u];
+    double den = 0.0;
+    for (int d = 0; d < D; ++d) num[d] = 0.0;
+    for (int dy = -rho; dy <= rho; ++dy) {
+        const int y = v + dy;
+        if (y < 0 || y >= H) continue;
+        for (int dx = -rho; dx <= rho; ++dx) {
+            const int x = u + dx;
+            if (x < 0 || x >= W) continue;
+            const double wd = exp(-(double)(dx * dx + dy * dy) / (gamma_d * gamma_d));
+            const double di = g[(size_t)y * W + x] - gc;
+            const double wr = exp(-(di * di) / (gamma_r * gamma_r));
+            const double *c = vol + ((size_t)y * W + x) * D;
+            for (int d = 0; d < D; ++d) num[d] += wd * wr * c[d];
+            den += wd * wr;
+        }
+    }
+    for (int d = 0; d < D; ++d) out[d] = num[d] / den;
+}
+
+/* Bilateral filter of one 2-D slice (tests use it with synthetic slices). */
+void orc_bilateral_slice(const double *slice, const double *g, int W, int H, int rho,
+                         double gamma_d, double gamma_r, double *out) {
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u)
+            out[(size_t)v * W + u] = orc_bilateral(slice, 1, 0, g, W, H, rho, gamma_d, gamma_r, u, v);
+}
+
+/* Sec. II-B-3: winner-take-all on a correlation (higher is better).
+ * Reading: ties go to the smallest d.  *gap (optional) = best - second best. */
+int orc_wta(const double *c, int D, double *gap) {
+    int best = 0;
+    for (int d = 1; d < D; ++d)
+        if (c[d] > c[best]) best = d;
+    if (gap) {
+        double second = -INFINITY;
+        for (int d = 0; d < D; ++d)
+            if (d != best && c[d] > second) second = c[d];
+        *gap = (D > 1) ? c[best] - second : INFINITY;
+    }
+    return best;
+}
+
+/* Eq. 12: parabola through (d-1, d, d+1) of the aggregated left costs.
+ * Reading: at d = 0 or d = D-1, or when the denominator is not negative
+ * (no strict interior maximum), d^s = d.  *den (optional) receives the
+ * denominator (0 at the ends). */
+double orc_parabola(const double *c, int D, int d, double *den) {
+    if (d <= 0 || d >= D - 1) {
+        if (den) *den = 0.0;
+        return (double)d;
+    }
+    const double cm = c[d - 1], c0 = c[d], cp = c[d + 1];
+    const double q = 2.0 * cm + 2.0 * cp - 4.0 * c0;
+    if (den) *den = q;
+    if (!(q < 0.0)) return (double)d;
+    return (double)d + (cm - cp) / q;
+}
+
+/* Eq. 11 with a tolerance: pixel u of a row passes iff its match u - l_ref
+ * lies in the image and the target map agrees there within lr_thresh. */
+int orc_lr_valid(int u, int lref, const int32_t *ltar_row, double lr_thresh) {
+    const int ur = u - lref;
+    if (ur < 0) return 0;
+    return fabs((double)(lref - ltar_row[ur])) <= lr_thresh;
+}
+
+/* Sec. II-C: undo the perspective transform, d = d^s + alpha0 + alpha1*v - delta. */
+double orc_postprocess(const orc_params *p, double ds, int v) {
+    return ds + orc_row_shift(p, v);
+}
+
+/* Sec. II-D: 3-D point of left pixel (u,v) with disparity dfull.
+ * Reading (the paper prints no formula): rectified pinhole pair in the left
+ * camera frame, Z = f T / d, X = (u - u0) Z / f, Y = (v - v0) Z / f.
+ * NaN when d is not finite or not positive. */
+void orc_reconstruct(const orc_params *p, double dfull, int u, int v, double *X, double *Y, double *Z) {
+    if (!isfinite(dfull) || dfull <= 0.0) {
+        *X = *Y = *Z = NAN;
+        return;
+    }
+    const double z = p->f_px * p->baseline / dfull;
+    *Z = z;
+    *X = ((double)u - p->u0) * z / p->f_px;
+    *Y = ((double)v - p->v0) * z / p->f_px;
+}
+
+/* Raw NCC volumes for rows [y0, y1).
+ * Left (reference) volume: cost_l(u,v,d) = NCC(left block u, right block u-d).
+ * Right (target) volume:   cost_r(u,v,d) = NCC(left block u+d, right block u).
+ * Both are evaluated from Eq. 3 directly; the identity of Sec. II-B-1,
+ * cost_r(u-d,v,d) = cost_l(u,v,d), is a property tests check. */
+static void cost_rows(const orc_params *p, const double *L, const double *R, int y0, int y1,
+                      double *cl, double *cr, int row_base) {
+    const int W = p->W, H = p->H, D = p->D;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int v = y0; v < y1; ++v) {
+        for (int u = 0; u < W; ++u) {
+            const size_t o = ((size_t)(v - row_base) * W + u) * D;
+            for (int d = 0; d < D; ++d) {
+                if (cl) cl[o + d] = orc_ncc(L, R, W, H, p->ncc_r, u, u - d, v);
+                if (cr) cr[o + d] = orc_ncc(L, R, W, H, p->ncc_r, u + d, u, v);
+            }
+        }
+    }
+}
+
+/* Full pipeline (Fig. 1 order) for output rows [row_begin, row_end).
+ * Returns 0 on success, -1 on bad arguments, -2 on allocation failure. */
+int orc_match(const orc_params *p, const uint8_t *il, const uint8_t *ir,
+              int row_begin, int row_end, orc_outputs *out) {
+    const int W = p->W, H = p->H, D = p->D, rho = p->agg_r;
+    if (W < 1 || H < 1 || D < 1 || p->ncc_r < 0 || rho < 0) return -1;
+    if (row_begin < 0) row_begin = 0;
+    if (row_end > H) row_end = H;
+    if (row_begin >= row_end) return 0;
+
+    const size_t npx = (size_t)W * H;
+    double *L = (double *)malloc(npx * sizeof(double));
+    double *R = (double *)malloc(npx * sizeof(double));
+    if (!L || !R) { free(L); free(R); return -2; }
+    for (size_t i = 0; i < npx; ++i) L[i] = il[i];
+    orc_warp(p, ir, R);
+    if (out->warped) memcpy(out->warped, R, npx * sizeof(double));
+
+    /* Block statistics (reported only; orc_ncc recomputes them by definition). */
+    if (out->mu_l || out->sig_l || out->mu_r || out->sig_r) {
+        #pragma omp parallel for schedule(static)
+        for (int v = row_begin; v < row_end; ++v)
+            for (int u = 0; u < W; ++u) {
+                double m, s;
+                const size_t i = (size_t)v * W + u;
+                orc_block_stats(L, W, H, p->ncc_r, u, v, &m, &s);
+                if (out->mu_l) out->mu_l[i] = m;
+                if (out->sig_l) out->sig_l[i] = s;
+                orc_block_stats(R, W, H, p->ncc_r, u, v, &m, &s);
+                if (out->mu_r) out->mu_r[i] = m;
+                if (out->sig_r) out->sig_r[i] = s;
+            }
+    }
+
+    /* Cost rows needed by the aggregation window of the requested band. */
+    const int cy0 = row_begin - rho < 0 ? 0 : row_begin - rho;
+    const int cy1 = row_end + rho > H ? H : row_end + rho;
+    double *cl, *cr;
+    int base;
+    if (out->cost_l && out->cost_r) {
+        cl = out->cost_l; cr = out->cost_r; base = 0;
+    } else {
+        const size_t n = (size_t)(cy1 - cy0) * W * D;
+        cl = (double *)malloc(n * sizeof(double));
+        cr = (double *)malloc(n * sizeof(double));
+        if (!cl || !cr) { free(cl); free(cr); free(L); free(R); return -2; }
+        base = cy0;
+    }
+    cost_rows(p, L, R, cy0, cy1, cl, cr, base);
+    if (base != 0) {
+        /* Copy the band back if the caller asked for one of the volumes. */
+        for (int v = cy0; v < cy1; ++v) {
+            const size_t src = (size_t)(v - base) * W * D, dst = (size_t)v * W * D;
+            if (out->cost_l) memcpy(out->cost_l + dst, cl + src, (size_t)W * D * sizeof(double));
+            if (out->cost_r) memcpy(out->cost_r + dst, cr + src, (size_t)W * D * sizeof(double));
+        }
+    }
+
+    /* Aggregation (Eqs. 8-10), WTA (Sec. II-B-3), parabola (Eq. 12). */
+    int32_t *lbl_l = out->lbl_l ? out->lbl_l : (int32_t *)malloc(npx * sizeof(int32_t));
+    int32_t *lbl_r = out->lbl_r ? out->lbl_r : (int32_t *)malloc(npx * sizeof(int32_t));
+    double *dsub = out->dsub ? out->dsub : (double *)malloc(npx * sizeof(double));
+    int err = (!lbl_l || !lbl_r || !dsub);
+    if (!err) {
+        /* Shift the volume pointers so that row v is addressed as v. */
+        const double *vl = cl - (size_t)base * W * D;
+        const double *vr = cr - (size_t)base * W * D;
+        #pragma omp parallel
+        {
+            double *num = (double *)malloc((size_t)D * sizeof(double));
+            double *al = (double *)malloc((size_t)D * sizeof(double));
+            double *ar = (double *)malloc((size_t)D * sizeof(double));
+            #pragma omp for schedule(dynamic, 1)
+            for (int v = row_begin; v < row_end; ++v) {
+                for (int u = 0; u < W; ++u) {
+                    const size_t i = (size_t)v * W + u;
+                    bilateral_all_d(vl, D, L, W, H, rho, p->gamma_d, p->gamma_r, u, v, num, al);
+                    bilateral_all_d(vr, D, R, W, H, rho, p->gamma_d, p->gamma_r, u, v, num, ar);
+                    if (out->agg_l) memcpy(out->agg_l + i * D, al, (size_t)D * sizeof(double));
+                    if (out->agg_r) memcpy(out->agg_r + i * D, ar, (size_t)D * sizeof(double));
+                    double g;
+                    lbl_l[i] = orc_wta(al, D, &g);
+                    if (out->gap_l) out->gap_l[i] = g;
+                    lbl_r[i] = orc_wta(ar, D, &g);
+                    if (out->gap_r) out->gap_r[i] = g;
+                    double q;
+                    dsub[i] = orc_parabola(al, D, lbl_l[i], &q);
+                    if (out->den_l) out->den_l[i] = q;
+                }
+            }
+            free(num); free(al); free(ar);
+        }
+        /* L-R check (Eq. 11), post-processing (Sec. II-C), 3-D (Sec. II-D). */
+        for (int v = row_begin; v < row_end; ++v) {
+            for (int u = 0; u < W; ++u) {
+                const size_t i = (size_t)v * W + u;
+                const int ok = orc_lr_valid(u, lbl_l[i], lbl_r + (size_t)v * W, p->lr_thresh);
+                const double df = ok ? orc_postprocess(p, dsub[i], v) : NAN;
+                if (out->valid) out->valid[i] = (uint8_t)ok;
+                if (out->dfull) out->dfull[i] = df;
+                if (out->xyz) {
+                    double X, Y, Z;
+                    orc_reconstruct(p, df, u, v, &X, &Y, &Z);
+                    out->xyz[i] = X; out->xyz[npx + i] = Y; out->xyz[2 * npx + i] = Z;
+                }
+            }
+        }
+    }
+    if (!out->lbl_l) free(lbl_l);
+    if (!out->lbl_r) free(lbl_r);
+    if (!out->dsub) free(dsub);
+    if (base != 0) { free(cl); free(cr); }
+    free(L); free(R);
+    return err ? -2 : 0;
+}
+
+/* Aggregated cost vector at one pixel, every NCC value evaluated on demand
+ * from Eq. 3 (no volume).  right = 0: reference view; right = 1: target view. */
+static void agg_vector_direct(const orc_params *p, const double *L, const double *R, int right,
+                              int u, int v, double *out) {
+    const int W = p->W, H = p->H, D = p->D, rho = p->agg_r;
+    const double *g = right ? R : L;
+    const double gc = g[(size_t)v * W + u];
+    double den = 0.0;
+    for (int d = 0; d < D; ++d) out[d] = 0.0;
+    for (int dy = -rho; dy <= rho; ++dy) {
+        const int y = v + dy;
+        if (y < 0 || y >= H) continue;
+        for (int dx = -rho; dx <= rho; ++dx) {
+            const int x = u + dx;
+            if (x < 0 || x >= W) continue;
+            const double wd = exp(-(double)(dx * dx + dy * dy) / (p->gamma_d * p->gamma_d));
+            const double di = g[(size_t)y * W + x] - gc;
+            const double wr = exp(-(di * di) / (p->gamma_r * p->gamma_r));
+            for (int d = 0; d < D; ++d) {
+                const double c = right ? orc_ncc(L, R, W, H, p->ncc_r, x + d, x, y)
+                                       : orc_ncc(L, R, W, H, p->ncc_r, x, x - d, y);
+                out[d] += wd * wr * c;
+            }
+            den += wd * wr;
+        }
+    }
+    for (int d = 0; d < D; ++d) out[d] /= den;
+}
+
+/* The pipeline at n sampled pixels (us[i], vs[i]), each computed on its own
+ * from the definitions (for checks at sizes where a full frame is slow).
+ * Outputs (any may be NULL) are per sample: l_ref, l_tar at the matched
+ * target pixel (or -1 if it lies outside), gaps, denominator, d^s, validity,
+ * post-processed disparity.  Returns 0, or -1/-2 as orc_match. */
+int orc_match_pixels(const orc_params *p, const uint8_t *il, const uint8_t *ir, int n,
+                     const int32_t *us, const int32_t *vs, int32_t *lbl_l, int32_t *lbl_r_match,
+                     double *gap_l, double *gap_r_match, double *den_l, double *dsub,
+                     uint8_t *valid, double *dfull) {
+    const int W = p->W, H = p->H, D = p->D;
+    if (W < 1 || H < 1 || D < 1) return -1;
+    const size_t npx = (size_t)W * H;
+    double *L = (double *)malloc(npx * sizeof(double));
+    double *R = (double *)malloc(npx * sizeof(double));
+    if (!L || !R) { free(L); free(R); return -2; }
+    for (size_t i = 0; i < npx; ++i) L[i] = il[i];
+    orc_warp(p, ir, R);
+    #pragma omp parallel
+    {
+        double *al = (double *)malloc((size_t)D * sizeof(double));
+        double *ar = (double *)malloc((size_t)D * sizeof(double));
+        #pragma omp for schedule(dynamic, 1)
+        for (int i = 0; i < n; ++i) {
+            const int u = us[i], v = vs[i];
+            double g, q;
+            agg_vector_direct(p, L, R, 0, u, v, al);
+            const int ll = orc_wta(al, D, &g);
+            if (gap_l) gap_l[i] = g;
+            const double ds = orc_parabola(al, D, ll, &q);
+            if (den_l) den_l[i] = q;
+            if (lbl_l) lbl_l[i] = ll;
+            if (dsub) dsub[i] = ds;
+            int lr = -1, ok = 0;
+            double gr = INFINITY;
+            if (u - ll >= 0) {
+                agg_vector_direct(p, L, R, 1, u - ll, v, ar);
+                lr = orc_wta(ar, D, &gr);
+                ok = fabs((double)(ll - lr)) <= p->lr_thresh;
+            }
+            if (lbl_r_match) lbl_r_match[i] = lr;
+            if (gap_r_match) gap_r_match[i] = gr;
+            if (valid) valid[i] = (uint8_t)ok;
+            if (dfull) dfull[i] = ok ? orc_postprocess(p, ds, v) : NAN;
+        }
+        free(al); free(ar);
+    }
+    free(L); free(R);
+    return 0;
+}
