@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the stereo hot path (Eq. 13 metric, Mde/s).
+
+One step = one sr_match over a seeded synthetic 1280x720 road pair with 64
+residual disparities, NCC 7x7, bilateral 11x11 (warp -> NCC volumes ->
+aggregation + WTA -> L-R check + post-processing), inputs resident in HBM.
+Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+band of rows of the same workload (the reference arm of this comparison).
+Under torchrun (N > 1) every rank matches its own frame (weak scaling, no
+collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpix·disp/s + fps at 720p×64 disp; fp16-volume/batched vs fp32 at stated error"
+UNIT = "Mpix·disp/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+L2_FLUSH_BYTES = 256 << 20
+
+
+def mdes(W: int, H: int, D: int, seconds: float) -> float:
+    """Eq. 13: millions of disparity evaluations per second."""
+    return W * H * D / seconds * 1e-6
+
+
+def agg_flops_per_launch(W, H, D, agg_r):
+    """Algorithmic work of one aggregation launch: one multiply and one add per
+    window tap per (u, v, d) (Eq. 8 numerator)."""
+    return 2 * (2 * agg_r + 1) ** 2 * W * H * D
+
+
+def _kernel_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("k_agg.cuh", "k_agg_d64.cu"):
+        with open(os.path.join(ROOT, "paper_1807_07433_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _stored_traffic():
+    """DRAM bytes per aggregation launch from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "agg_wta_1280x720x64.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*;\s*kernel_sha:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != _kernel_sha():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_07433_gb300 import sr, synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W, H, D = w.scene.W, w.scene.H, w.D
+    left, right, _ = synth.make_pair(w.scene)
+    stream = torch.cuda.current_stream(dev)
+
+    dl = torch.from_numpy(left).to(dev)
+    dr = torch.from_numpy(right).to(dev)
+    disp = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    m = sr.Matcher(W, H, D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh, stream=stream)
+    m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+    kpm = sr.sr_kernels_per_match(m.ctx)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        m.match(dl, dr, disp)
+    torch.cuda.synchronize()
+
+    sr.sr_set_profiling(m.ctx, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_rows = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush outside the timed events
+            starts[k].record(stream)
+            m.match(dl, dr, disp)
+            ends[k].record(stream)
+            stage_rows.append(sr.sr_stage_times(m.ctx))   # synchronises the stream
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    sr.sr_set_profiling(m.ctx, False)
+
+    # End to end through the public C ABI with pinned host buffers.
+    hl = torch.from_numpy(left).pin_memory()
+    hr = torch.from_numpy(right).pin_memory()
+    hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    for _ in range(max(2, args.warmup)):
+        sr.sr_match_host(m.ctx, hl, hr, hd)
+    if ws > 1:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        sr.sr_match_host(m.ctx, hl, hr, hd)
+    torch.cuda.synchronize()
+    e_s = time.perf_counter() - e0
+    te = torch.tensor([e_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e_s = float(te.item())
+    valid_frac = float(np.isfinite(hd.numpy()).mean())
+    m.close()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+
+    ms_step = total_ms_max / args.steps
+    agg_ms = [0.5 * (r["agg_ref"] + r["agg_tgt"]) for r in stage_rows]
+    agg_avg_ms = sum(agg_ms) / len(agg_ms)
+    flops = agg_flops_per_launch(W, H, D, w.agg_r)
+    achieved = flops / (agg_avg_ms * 1e-3) / 1e12
+    stages = {k: round(sum(r[k] for r in stage_rows) / len(stage_rows), 5) for k in stage_rows[0]}
+    line = {
+        "metric": METRIC, "value": round(mdes(W, H, D, ms_step * 1e-3) * ws, 2), "unit": UNIT,
+        "fps": round(1000.0 / ms_step * ws, 2),
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded textured road plane with potholes and grooves (generator "
+                "paper_1807_07433_gb300/synth.py, seed 2); stands in for the paper's ZED road data",
+        "config": {"workload": w.name, "W": W, "H": H, "D": D, "ncc_window": 2 * w.ncc_r + 1,
+                   "bilateral_window": 2 * w.agg_r + 1, "gamma_d": w.gamma_d,
+                   "gamma_r": w.gamma_r, "delta": w.delta, "form": "staged fp32 volumes",
+                   "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB memset)",
+                   "parallelism": f"replicas x{ws} (independent frames)"},
+        "roofline": {"bound": "alu", "kernel": "k_agg_wta (reference+target mean)",
+                     "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                     "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "flops_per_launch": flops, "launch_ms": round(agg_avg_ms, 5),
+                     "traffic": _stored_traffic()},
+        "stages_ms": stages,
+        "e2e": {"value": round(mdes(W, H, D, e_s / args.steps), 2), "unit": UNIT,
+                "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 4 * W * H,
+                "api": "sr_match_host (pinned host buffers)"},
+        "gpu_launches": kpm * args.steps,
+        "valid_fraction": round(valid_frac, 4),
+        "wall_s_timed_region": round(wall, 3),
+    }
+    clk_sum = clk.summary()
+    line["clocks"] = clk_sum
+    return line
+
+
+def oracle_sample(w, target_s: float, rows_hint: int | None = None):
+    """Time the FP64 oracle on a band of output rows sized for about
+    target_s seconds; returns (Mde/s, seconds, rows, cores)."""
+    import oracle
+    from paper_1807_07433_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_num_threads(cores)
+    left, right, _ = synth.make_pair(w.scene)
+    p = oracle.Params(W=w.scene.W, H=w.scene.H, D=w.D, ncc_r=w.ncc_r, agg_r=w.agg_r,
+                      gamma_d=w.gamma_d, gamma_r=w.gamma_r, lr_thresh=w.lr_thresh,
+                      alpha0=w.scene.alpha0, alpha1=w.scene.alpha1, delta=w.delta)
+    r0 = 0
+    if rows_hint is None:
+        probe = min(16, w.scene.H)
+        t0 = time.perf_counter()
+        oracle.match(p, left, right, rows=(0, probe), want=("dfull",))
+        t_probe = time.perf_counter() - t0
+        rows = int(max(probe, min(w.scene.H, probe * target_s / max(t_probe, 1e-6))))
+    else:
+        rows = rows_hint
+    t0 = time.perf_counter()
+    oracle.match(p, left, right, rows=(r0, r0 + rows), want=("dfull",))
+    dt = time.perf_counter() - t0
+    return mdes(w.scene.W, rows, w.D, dt), dt, (r0, r0 + rows), oracle.num_threads()
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    # one probe sizes the band; each timed step re-runs the band
+    val, dt, rows, cores = oracle_sample(w, target_s=min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(w, 0, rows_hint=rows[1] - rows[0])
+    times = []
+    for _ in range(args.steps):
+        v, dt, _, _ = oracle_sample(w, 0, rows_hint=rows[1] - rows[0])
+        times.append(dt)
+    per = sum(times) / len(times)
+    value = mdes(w.scene.W, rows[1] - rows[0], w.D, per)
+    sample = (f"output rows {rows[0]}..{rows[1] - 1} of the {w.scene.W}x{w.scene.H}x{w.D} frame "
+              f"(+{w.agg_r} halo rows of NCC each side), FP64 oracle, OpenMP")
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(per * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (same seeded scene as ours)",
+        "config": {"workload": w.name, "W": w.scene.W, "H": w.scene.H, "D": w.D,
+                   "ncc_window": 2 * w.ncc_r + 1, "bilateral_window": 2 * w.agg_r + 1},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    from paper_1807_07433_gb300 import synth
+    w = synth.C2
+
+    if args.impl == "reference":
+        line = run_reference(args, w)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    from paper_1807_07433_gb300 import sr
+    if not os.path.exists(sr.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    line = run_ours(args, w)
+    if line is None:
+        return
+    ws = line["n_gpus"]
+    if ws == 1 and not args.no_cpu_baseline:
+        val, dt, rows, cores = oracle_sample(w, target_s=15.0)
+        line["cpu_baseline"] = {
+            "value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"output rows {rows[0]}..{rows[1] - 1} of the same frame, {dt:.1f} s, "
+                      f"FP64 oracle with OpenMP"}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

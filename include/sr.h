@@ -1,0 +1,187 @@
+/*
+ * sr.h -- C ABI of the GB300 road-surface stereo library (libsr.so).
+ *
+ * Method: Fan et al., "Real-Time Stereo Vision for Road Surface 3-D
+ * Reconstruction" (arXiv 1807.07433), Fig. 1 pipeline:
+ *   perspective transformation of the target image (Sec. II-A, Eq. 2)
+ *   -> block NCC costs in a reference and a target cost volume (Eqs. 3-5,
+ *      Sec. II-B-1)
+ *   -> bilateral cost aggregation (Eqs. 8-10)
+ *   -> winner-take-all on both volumes (Sec. II-B-3)
+ *   -> left-right consistency check (Eq. 11) and parabola subpixel
+ *      refinement (Eq. 12)
+ *   -> post-processing back to full disparity (Sec. II-C)
+ *   -> 3-D reconstruction (Sec. II-D).
+ *
+ * Conventions shared by every entry point:
+ *   - Images are 8-bit grayscale, row-major, W columns by H rows.  The left
+ *     image is the reference view, the right image the target view.
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; h_*
+ *     are host pointers owned by the caller.  The library never frees or
+ *     retains a caller pointer beyond the call (or, for asynchronous calls,
+ *     beyond the completion of the work queued on the context's stream).
+ *   - All GPU work is queued asynchronously on the stream given to
+ *     sr_create (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream).  Functions that write host memory synchronise that stream.
+ *   - No function aborts, prints or throws.  Every function returns an
+ *     sr_status; sr_status_str() names it.  A CUDA error is reported as
+ *     SR_ERR_CUDA; the text of the last CUDA error of a context is kept and
+ *     returned by sr_last_error().
+ *   - Disparities: the search covers residual disparities 0..D-1 in the
+ *     transformed (warped) domain; full disparity = residual + alpha0 +
+ *     alpha1*v - delta (Sec. II-C).
+ *   - The library is single-GPU: a context lives on the device that was
+ *     current when it was created, and every call must be made with that
+ *     device current.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SR_OK = 0,
+    SR_ERR_INVALID_ARG = 1,   /* null pointer, bad size or pitch, ... */
+    SR_ERR_UNSUPPORTED = 2,   /* parameter outside the compiled kernel set */
+    SR_ERR_OOM = 3,           /* device or host allocation failed */
+    SR_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    SR_ERR_STATE = 5,         /* call out of order (e.g. no camera set) */
+    SR_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} sr_status;
+
+/* Storage type of the staged cost volumes.  All arithmetic is FP32. */
+typedef enum { SR_VOL_F32 = 0, SR_VOL_F16 = 1, SR_VOL_BF16 = 2 } sr_vol_dtype;
+
+/* Method parameters, fixed for the lifetime of a context.
+ *   width, height  image size W x H, 1..16384 each.
+ *   max_disp       D, residual disparities searched, 0..D-1 (Sec. II-B-3);
+ *                  supported: 16, 32, 64.
+ *   ncc_radius     NCC block radius (the rho-script of Eq. 3), block
+ *                  (2r+1)^2; supported 1..5.
+ *   agg_radius     bilateral window radius (rho of Eq. 8); supported 1..7.
+ *   gamma_d        Eq. 9 spatial constant, > 0 (exp(-r^2/gamma_d^2)).
+ *   gamma_r        Eq. 10 intensity constant on the 0..255 scale, > 0.
+ *   lr_thresh      tolerance of the Eq. 11 consistency check in pixels,
+ *                  >= 0 (Eq. 11 itself is 0).
+ *   vol_dtype      storage of the staged cost volumes (see sr_vol_dtype).
+ */
+typedef struct {
+    int width, height;
+    int max_disp;
+    int ncc_radius;
+    int agg_radius;
+    float gamma_d, gamma_r;
+    float lr_thresh;
+    sr_vol_dtype vol_dtype;
+} sr_params;
+
+typedef struct sr_ctx sr_ctx;   /* opaque; owns only its device scratch */
+
+/* Create a context on the current device.  cuda_stream is the cudaStream_t
+ * all work is queued on (NULL = legacy default stream).  Allocates the
+ * context's scratch: warped image, block statistics, the two cost volumes
+ * and the per-pixel maps (about W*H*(2*D*4 + 40) bytes for FP32 volumes).
+ * Errors: SR_ERR_INVALID_ARG (null out, non-positive sizes or constants),
+ * SR_ERR_UNSUPPORTED (D, radii outside the supported set), SR_ERR_OOM,
+ * SR_ERR_CUDA.  On error *out is set to NULL. */
+sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out);
+
+/* Release the context and its scratch (synchronises its stream first).
+ * NULL is accepted and ignored. */
+sr_status sr_destroy(sr_ctx *ctx);
+
+/* Road-plane model of Eq. 2 and the offset of Sec. II-A: target row v is
+ * shifted alpha0 + alpha1*v - delta pixels to the right before matching.
+ * Units: alpha0 and delta in pixels, alpha1 in pixels per row.  All
+ * finite values are accepted; the default is (0, 0, 0). */
+sr_status sr_set_plane(sr_ctx *ctx, double alpha0, double alpha1, double delta);
+
+/* Camera of Sec. II-D: focal length f_px (pixels), baseline (any length
+ * unit, XYZ comes out in that unit) and principal point (u0, v0) in pixels.
+ * Required before sr_reconstruct. */
+sr_status sr_set_camera(sr_ctx *ctx, double f_px, double baseline, double u0, double v0);
+
+/* Disparity estimation, Secs. II-A..II-C (the hot path).
+ *   d_left, d_right  W x H uint8 images, row pitch pitch_bytes (>= W).
+ *   d_disp           W x H float (dense, pitch W): full disparity of each
+ *                    left pixel, NaN where the L-R check (Eq. 11) fails.
+ *   d_wta_or_null    optional W x H int16 (dense): the integer WTA residual
+ *                    disparity l_ref of the reference view.
+ * Asynchronous on the context's stream.  Errors: SR_ERR_INVALID_ARG for
+ * null images/output or pitch < W, SR_ERR_CUDA for a failed launch. */
+sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
+                   float *d_disp, int16_t *d_wta_or_null);
+
+/* sr_match with host buffers: copies h_left/h_right (W x H, dense) to the
+ * device, runs sr_match, copies the disparity map back into h_disp (W x H
+ * float) and synchronises the stream.  Pinned host memory makes the copies
+ * asynchronous; pageable memory works but is slower.  Uses staging buffers
+ * owned by the context (allocated on first use). */
+sr_status sr_match_host(sr_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
+                        float *h_disp);
+
+/* 3-D reconstruction, Sec. II-D, for the left pixels of a full-disparity
+ * map d_disp (W x H float, as written by sr_match).  d_xyz receives three
+ * planes of W x H floats (X, then Y, then Z) in the camera frame of the
+ * left camera: Z = f*B/d, X = (u-u0)*Z/f, Y = (v-v0)*Z/f; NaN where d is
+ * NaN or not positive.  Asynchronous.  SR_ERR_STATE if no camera is set. */
+sr_status sr_reconstruct(sr_ctx *ctx, const float *d_disp, float *d_xyz);
+
+/* Intermediate arrays of the last sr_match, for inspection and tests.
+ * which selects the array; its device layout and element type are fixed:
+ *   SR_BUF_WARPED     float [H][W]        warped target i_r' (Sec. II-A)
+ *   SR_BUF_MU_L       float [H][W]        block mean of i_l (Eq. 4)
+ *   SR_BUF_INV_L      float [H][W]        1/(n*sigma_l), 0 for a flat block
+ *   SR_BUF_MU_R       float [H][W]        block mean of i_r'
+ *   SR_BUF_INV_R      float [H][W]        1/(n*sigma_r), 0 for a flat block
+ *   SR_BUF_COST_L     float [H][W][D]     reference NCC volume (Eq. 3)
+ *   SR_BUF_COST_R     float [H][W][D]     target NCC volume
+ *   SR_BUF_AGG_L      float [H][W][D]     aggregated reference volume (Eq. 8),
+ *   SR_BUF_AGG_R      float [H][W][D]     ... and target volume; these two are
+ *                                          only written while the debug flag
+ *                                          SR_DEBUG_KEEP_AGG is set
+ *   SR_BUF_WTA_L      int16 [H][W]        l_ref
+ *   SR_BUF_WTA_R      int16 [H][W]        l_tar
+ *   SR_BUF_DSUB       float [H][W]        subpixel residual d^s (Eq. 12)
+ * The array is copied (synchronously) into dst, a host or device pointer of
+ * at least the array's size, which *bytes_inout gives on input and receives
+ * on output.  Volumes stored in FP16/BF16 are widened to float.
+ * Errors: SR_ERR_INVALID_ARG (unknown which, dst too small),
+ * SR_ERR_STATE (array not produced, e.g. AGG without the debug flag). */
+typedef enum {
+    SR_BUF_WARPED = 0, SR_BUF_MU_L, SR_BUF_INV_L, SR_BUF_MU_R, SR_BUF_INV_R,
+    SR_BUF_COST_L, SR_BUF_COST_R, SR_BUF_AGG_L, SR_BUF_AGG_R,
+    SR_BUF_WTA_L, SR_BUF_WTA_R, SR_BUF_DSUB
+} sr_buffer;
+sr_status sr_get_buffer(sr_ctx *ctx, sr_buffer which, void *dst, size_t *bytes_inout);
+
+/* Debug flags (bit set).  SR_DEBUG_KEEP_AGG makes sr_match also store both
+ * aggregated volumes (allocated on first use, 2*W*H*D floats). */
+#define SR_DEBUG_KEEP_AGG 1
+sr_status sr_set_debug(sr_ctx *ctx, int flags);
+
+/* Per-stage timing.  While enabled, sr_match records a CUDA event before
+ * and after each stage on the context's stream.  sr_stage_times
+ * synchronises the stream and writes, for the most recent sr_match, the
+ * duration in milliseconds of each stage into ms[0..n) in the order of
+ * sr_stage_names(); it returns the number of stages in *count. */
+sr_status sr_set_profiling(sr_ctx *ctx, int enable);
+sr_status sr_stage_times(sr_ctx *ctx, float *ms, int n, int *count);
+const char *sr_stage_names(void);   /* comma-separated stage names */
+
+/* Number of kernel launches one sr_match queues (for launch accounting). */
+int sr_kernels_per_match(const sr_ctx *ctx);
+
+const char *sr_status_str(sr_status s);
+const char *sr_last_error(const sr_ctx *ctx);
+const char *sr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR_H */

@@ -1,0 +1,8 @@
+// k_agg_d16.cu -- Eqs. 8-12 aggregation/WTA kernels instantiated for D = 16.
+#include "k_agg.cuh"
+
+namespace sr {
+cudaError_t launch_agg_d16(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, cudaStream_t st) {
+    return agg_launch_d<16>(vol, gl, pitch, gf, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
+}
+}  // namespace sr

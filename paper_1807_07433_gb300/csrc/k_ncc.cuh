@@ -1,0 +1,169 @@
+// k_ncc.cuh -- Eq. 3 NCC cost volumes.
+//
+// One thread per output pixel (u,v) computes all D costs of that pixel.
+//   reference volume: c(u,v,d) = NCC(left block at u, warped-target block at u-d)
+//   target volume:    c(u,v,d) = NCC(left block at u+d, warped-target block at u)
+// (the two volumes of Sec. II-B-1; c of the reference volume at (u,v,d) equals
+// c of the target volume at (u-d,v,d)).
+//
+// Numerics.  The numerator of Eq. 3, sum(i_l i_r) - n mu_l mu_r, equals
+// sum((f - mu_f) * (s - K)) for ANY constant K when f is the block that stays
+// fixed while d varies and s the block that slides.  The fixed block is
+// centred once per pixel (49 registers for a 7x7 block), the sliding block is
+// offset by K = 128, so no large terms cancel.  The centred values a_i carry
+// the rounding error e of the FP32 mean; to first order it adds
+// -e * sum(s - K) = (sum a_i) * n(mu_s - K) / n, so the kernel subtracts
+// (sum a_i) * (mu_s - K) using the sliding block's mean.  The result keeps
+// ~1e-7 relative accuracy even on near-flat blocks, where the textbook form
+// loses ~1e-5 and the uncorrected centred form ~1e-3.
+//
+// Work per pixel: the dot products of all D disparities are organised by
+// sliding-image COLUMN: column c contributes sum_oy a[oy][ox] * s(c, v+oy) to
+// disparity d = (u - c) + ox - r (reference) or (c - u) - ox + r (target) for
+// each block column ox.  Each column of the sliding block is read from shared
+// memory once (2r+1 loads) and feeds up to (2r+1)^2 FMAs, so the kernel is
+// FMA-bound rather than shared-memory-bound.  Disparities are processed in
+// chunks of DC so that the accumulators stay in registers.
+//
+// Tiles: 32 x 4 output pixels per CTA (128 threads); the fixed image tile and
+// the sliding image tile (widened by D-1 columns) are staged in shared memory
+// with clamp-to-edge reads, as the block definition of Eqs. 3-5 requires.
+#pragma once
+#include "sr_internal.cuh"
+
+namespace sr {
+
+constexpr int kNccTX = 32, kNccTY = 4, kNccThreads = kNccTX * kNccTY;
+
+template <int RN, int D, bool TARGET>
+__global__ void __launch_bounds__(kNccThreads)
+k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
+      const float *__restrict__ mu_l, const float *__restrict__ inv_l,
+      const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
+      float *__restrict__ vol) {
+    constexpr int B = 2 * RN + 1;
+    constexpr int FW = kNccTX + 2 * RN;          // fixed tile width
+    constexpr int SW = kNccTX + 2 * RN + D - 1;  // sliding tile width
+    constexpr int TH = kNccTY + 2 * RN;          // tile height
+    constexpr int DC = D < 32 ? D : 32;          // disparity chunk held in registers
+    __shared__ float fix_s[TH][FW];
+    __shared__ float sld_s[TH][SW];
+
+    const int x0 = blockIdx.x * kNccTX, y0 = blockIdx.y * kNccTY;
+    const int tid = threadIdx.x;
+    const int WE = W + D - 1;
+
+    // Stage the fixed and sliding tiles (clamp-to-edge).
+    const int fx0 = x0 - RN;
+    const int sx0 = TARGET ? x0 - RN : x0 - RN - (D - 1);
+    for (int i = tid; i < TH * FW; i += kNccThreads) {
+        const int r = i / FW, c = i % FW;
+        const int y = clampi(y0 - RN + r, 0, H - 1), x = clampi(fx0 + c, 0, W - 1);
+        fix_s[r][c] = TARGET ? rw[(size_t)y * W + x] : (float)left[(size_t)y * pitch + x];
+    }
+    for (int i = tid; i < TH * SW; i += kNccThreads) {
+        const int r = i / SW, c = i % SW;
+        const int y = clampi(y0 - RN + r, 0, H - 1), x = clampi(sx0 + c, 0, W - 1);
+        const float val = TARGET ? (float)left[(size_t)y * pitch + x] : rw[(size_t)y * W + x];
+        sld_s[r][c] = val - kNccOffset;
+    }
+    __syncthreads();
+
+    const int tx = tid % kNccTX, ty = tid / kNccTX;
+    const int u = x0 + tx, v = y0 + ty;
+    if (u >= W || v >= H) return;
+
+    // Statistics rows (block centres extended by D-1 columns, see launch_stats):
+    // the fixed block sits at u, the sliding block at u+d (target) / u-d (reference).
+    const size_t rowo = (size_t)v * WE;
+    const float *mu_f = TARGET ? mu_r + rowo + u + D - 1 : mu_l + rowo + u;
+    const float *inv_fp = TARGET ? inv_r + rowo + u + D - 1 : inv_l + rowo + u;
+    const float *mu_s_row = TARGET ? mu_l + rowo + u : mu_r + rowo + u + D - 1;
+    const float *inv_s_row = TARGET ? inv_l + rowo + u : inv_r + rowo + u + D - 1;
+
+    // Centred fixed block and the sum of its (rounded) centred values.
+    const float m = *mu_f;
+    float a[B][B];
+    float sa = 0.0f;
+#pragma unroll
+    for (int oy = 0; oy < B; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < B; ++ox) {
+            a[oy][ox] = fix_s[ty + oy][tx + ox] - m;
+            sa += a[oy][ox];
+        }
+
+    // n/(n sigma_f) of the fixed block (Eq. 3 divides n*cov by n*sigma_f*sigma_s).
+    constexpr float n = (float)(B * B);
+    const float inv_f = n * *inv_fp;
+    float *out = vol + ((size_t)v * W + u) * D;
+
+#pragma unroll 1
+    for (int d0 = 0; d0 < D; d0 += DC) {
+        float acc[DC];
+#pragma unroll
+        for (int i = 0; i < DC; ++i) acc[i] = 0.0f;
+        // Sliding column c = u - k (reference) or u + k (target), k = d + (ox - RN)
+        // resp. d - (ox - RN); k spans [d0 - RN, d0 + DC - 1 + RN].
+#pragma unroll
+        for (int kk = 0; kk < DC + 2 * RN; ++kk) {
+            const int k = d0 - RN + kk;
+            const int sc = TARGET ? tx + k + RN : tx - k + RN + D - 1;
+            float col[B];
+#pragma unroll
+            for (int oy = 0; oy < B; ++oy) col[oy] = sld_s[ty + oy][sc];
+#pragma unroll
+            for (int ox = 0; ox < B; ++ox) {
+                const int dl = TARGET ? kk - ox : kk + ox - 2 * RN;   // d - d0
+                if (dl >= 0 && dl < DC) {
+                    float s = acc[dl];
+#pragma unroll
+                    for (int oy = 0; oy < B; ++oy) s = fmaf(a[oy][ox], col[oy], s);
+                    acc[dl] = s;
+                }
+            }
+        }
+        // Mean correction, Eq. 3 denominator, store the chunk.
+        float cst[DC];
+#pragma unroll
+        for (int i = 0; i < DC; ++i) {
+            const int d = d0 + i;
+            const int so = TARGET ? d : -d;
+            const float num = fmaf(-sa, mu_s_row[so] - kNccOffset, acc[i]);
+            cst[i] = num * inv_f * inv_s_row[so];
+        }
+#pragma unroll
+        for (int i = 0; i < DC; i += 4)
+            *reinterpret_cast<float4 *>(out + d0 + i) =
+                make_float4(cst[i], cst[i + 1], cst[i + 2], cst[i + 3]);
+    }
+}
+
+template <int RN, int D>
+cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const float *rw,
+                         const float *mu_l, const float *inv_l, const float *mu_r,
+                         const float *inv_r, int W, int H, float *vol, cudaStream_t st) {
+    const dim3 grid((W + kNccTX - 1) / kNccTX, (H + kNccTY - 1) / kNccTY);
+    if (target)
+        k_ncc<RN, D, true><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
+    else
+        k_ncc<RN, D, false><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t ncc_launch_d(bool target, const uint8_t *left, int pitch, const float *rw,
+                         const float *mu_l, const float *inv_l, const float *mu_r,
+                         const float *inv_r, int W, int H, int ncc_r, float *vol,
+                         cudaStream_t st) {
+    switch (ncc_r) {
+        case 1: return ncc_launch_t<1, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 2: return ncc_launch_t<2, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 3: return ncc_launch_t<3, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 4: return ncc_launch_t<4, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 5: return ncc_launch_t<5, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sr

@@ -1,0 +1,182 @@
+// k_pixel.cu -- per-pixel stages: perspective transformation (Sec. II-A),
+// block statistics (Eqs. 4-5), L-R check + post-processing (Eq. 11,
+// Sec. II-C) and 3-D reconstruction (Sec. II-D).  All are O(W*H) and
+// bandwidth-trivial next to the cost volumes; one thread per output pixel,
+// 2-D blocks of 32x8 so that a warp reads 32 consecutive pixels of a row.
+#include <math.h>
+
+#include "sr_internal.cuh"
+
+namespace sr {
+namespace {
+
+constexpr int kBX = 32, kBY = 8;
+
+__global__ void k_warp(const uint8_t *__restrict__ right, int pitch, int W, int H, double alpha0,
+                       double alpha1, double delta, float *__restrict__ rw) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (x >= W || v >= H) return;
+    // s(v) of Sec. II-A in double: it also feeds Sec. II-C post-processing.
+    const double s = alpha0 + alpha1 * (double)v - delta;
+    double k = floor(s);
+    const float w = (float)(s - k);
+    k = fmin(fmax(k, -2.0 * W - 2.0), 2.0 * W + 2.0);   // beyond this every read clamps
+    const int ki = (int)k;
+    const uint8_t *row = right + (size_t)v * pitch;
+    const float a = row[clampi(x - ki, 0, W - 1)];
+    const float b = row[clampi(x - ki - 1, 0, W - 1)];
+    rw[(size_t)v * W + x] = fmaf(w, b - a, a);        // (1-w) a + w b
+}
+
+// Left block statistics from exact integer sums: n^2 sigma^2 = n S2 - S^2.
+// Centres x in [0, W+D-1) (the target volume needs left blocks at u+d).
+template <int RN>
+__global__ void k_stats_left(const uint8_t *__restrict__ left, int pitch, int W, int H, int WE,
+                             float *__restrict__ mu, float *__restrict__ inv) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (x >= WE || v >= H) return;
+    constexpr int n = (2 * RN + 1) * (2 * RN + 1);
+    unsigned s = 0, s2 = 0;
+#pragma unroll
+    for (int j = -RN; j <= RN; ++j) {
+        const uint8_t *row = left + (size_t)clampi(v + j, 0, H - 1) * pitch;
+#pragma unroll
+        for (int i = -RN; i <= RN; ++i) {
+            const unsigned val = row[clampi(x + i, 0, W - 1)];
+            s += val;
+            s2 += val * val;
+        }
+    }
+    const long long q = (long long)n * s2 - (long long)s * s;   // n^2 var, exact
+    const float var = (float)q / (float)(n * n);
+    inv[(size_t)v * WE + x] = (var < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)q);
+    mu[(size_t)v * WE + x] = (float)s / (float)n;
+}
+
+// Warped-target block statistics, two-pass (mean, then centred squares).
+// Centres x in [-(D-1), W), stored at x + D - 1.
+template <int RN>
+__global__ void k_stats_right(const float *__restrict__ rw, int W, int H, int D, int WE,
+                              float *__restrict__ mu, float *__restrict__ inv) {
+    const int xi = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (xi >= WE || v >= H) return;
+    const int x = xi - (D - 1);
+    constexpr int n = (2 * RN + 1) * (2 * RN + 1);
+    // Mean: row sums of (value - 128) then their sum, so that no partial sum
+    // grows past a few thousand (FP32 rounding ~1e-6 of an intensity).
+    float val[2 * RN + 1][2 * RN + 1];
+    float s = 0.0f;
+#pragma unroll
+    for (int j = -RN; j <= RN; ++j) {
+        const float *row = rw + (size_t)clampi(v + j, 0, H - 1) * W;
+        float rs = 0.0f;
+#pragma unroll
+        for (int i = -RN; i <= RN; ++i) {
+            val[j + RN][i + RN] = row[clampi(x + i, 0, W - 1)];
+            rs += val[j + RN][i + RN] - kNccOffset;
+        }
+        s += rs;
+    }
+    const float m = kNccOffset + s / (float)n;
+    float q = 0.0f;
+#pragma unroll
+    for (int j = 0; j <= 2 * RN; ++j)
+#pragma unroll
+        for (int i = 0; i <= 2 * RN; ++i) {
+            const float c = val[j][i] - m;
+            q = fmaf(c, c, q);
+        }
+    // q = n sigma^2; 1/(n sigma) = 1/sqrt(n q)
+    inv[(size_t)v * WE + xi] = (q / (float)n < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)n * q);
+    mu[(size_t)v * WE + xi] = m;
+}
+
+__global__ void k_lrc_post(const int16_t *__restrict__ lbl_l, const int16_t *__restrict__ lbl_r,
+                           const float *__restrict__ dsub, int W, int H, double alpha0,
+                           double alpha1, double delta, float lr_thresh, float *__restrict__ disp,
+                           int16_t *__restrict__ wta_out) {
+    const int u = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (u >= W || v >= H) return;
+    const size_t i = (size_t)v * W + u;
+    const int l = lbl_l[i];
+    const int ur = u - l;
+    bool ok = false;
+    if (ur >= 0) ok = fabsf((float)(l - (int)lbl_r[(size_t)v * W + ur])) <= lr_thresh;
+    const double s = alpha0 + alpha1 * (double)v - delta;
+    disp[i] = ok ? (float)((double)dsub[i] + s) : __int_as_float(0x7fc00000);
+    if (wta_out) wta_out[i] = (int16_t)l;
+}
+
+__global__ void k_xyz(const float *__restrict__ disp, int W, int H, float f, float fb, float u0,
+                      float v0, float *__restrict__ xyz) {
+    const int u = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (u >= W || v >= H) return;
+    const size_t i = (size_t)v * W + u, npx = (size_t)W * H;
+    const float d = disp[i];
+    float X, Y, Z;
+    if (!(d > 0.0f) || isinf(d)) {
+        X = Y = Z = __int_as_float(0x7fc00000);
+    } else {
+        Z = fb / d;
+        X = ((float)u - u0) * Z / f;
+        Y = ((float)v - v0) * Z / f;
+    }
+    xyz[i] = X;
+    xyz[npx + i] = Y;
+    xyz[2 * npx + i] = Z;
+}
+
+dim3 grid_for(int w, int h) { return dim3((w + kBX - 1) / kBX, (h + kBY - 1) / kBY); }
+
+}  // namespace
+
+cudaError_t launch_warp(const uint8_t *right, int pitch, int W, int H, double alpha0,
+                        double alpha1, double delta, float *rw, cudaStream_t st) {
+    k_warp<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(right, pitch, W, H, alpha0, alpha1, delta, rw);
+    return cudaGetLastError();
+}
+
+template <int RN>
+static void stats_rn(const uint8_t *left, int pitch, const float *rw, int W, int H, int D,
+                     float *mu_l, float *inv_l, float *mu_r, float *inv_r, cudaStream_t st) {
+    const int WE = W + D - 1;
+    k_stats_left<RN><<<grid_for(WE, H), dim3(kBX, kBY), 0, st>>>(left, pitch, W, H, WE, mu_l, inv_l);
+    k_stats_right<RN><<<grid_for(WE, H), dim3(kBX, kBY), 0, st>>>(rw, W, H, D, WE, mu_r, inv_r);
+}
+
+cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W, int H, int D,
+                         int ncc_r, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
+                         cudaStream_t st) {
+    switch (ncc_r) {
+        case 1: stats_rn<1>(left, pitch, rw, W, H, D, mu_l, inv_l, mu_r, inv_r, st); break;
+        case 2: stats_rn<2>(left, pitch, rw, W, H, D, mu_l, inv_l, mu_r, inv_r, st); break;
+        case 3: stats_rn<3>(left, pitch, rw, W, H, D, mu_l, inv_l, mu_r, inv_r, st); break;
+        case 4: stats_rn<4>(left, pitch, rw, W, H, D, mu_l, inv_l, mu_r, inv_r, st); break;
+        case 5: stats_rn<5>(left, pitch, rw, W, H, D, mu_l, inv_l, mu_r, inv_r, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,
+                            int H, double alpha0, double alpha1, double delta, float lr_thresh,
+                            float *disp, int16_t *wta_out, cudaStream_t st) {
+    k_lrc_post<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(lbl_l, lbl_r, dsub, W, H, alpha0, alpha1,
+                                                         delta, lr_thresh, disp, wta_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xyz(const float *disp, int W, int H, double f_px, double baseline, double u0,
+                       double v0, float *xyz, cudaStream_t st) {
+    k_xyz<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(disp, W, H, (float)f_px,
+                                                    (float)(f_px * baseline), (float)u0,
+                                                    (float)v0, xyz);
+    return cudaGetLastError();
+}
+
+}  // namespace sr

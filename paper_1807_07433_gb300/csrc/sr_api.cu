@@ -1,0 +1,363 @@
+// sr_api.cu -- the C ABI of include/sr.h: context, argument checks, scratch
+// ownership, stage sequencing on the caller's stream, timing and errors.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/sr.h"
+#include "sr_internal.cuh"
+
+namespace sr {
+cudaError_t launch_ncc_d16(bool, const uint8_t *, int, const float *, const float *, const float *,
+                           const float *, const float *, int, int, int, float *, cudaStream_t);
+cudaError_t launch_ncc_d32(bool, const uint8_t *, int, const float *, const float *, const float *,
+                           const float *, const float *, int, int, int, float *, cudaStream_t);
+cudaError_t launch_ncc_d64(bool, const uint8_t *, int, const float *, const float *, const float *,
+                           const float *, const float *, int, int, int, float *, cudaStream_t);
+cudaError_t launch_agg_d16(const float *, const uint8_t *, int, const float *, int, int, int, float,
+                           float, int16_t *, float *, float *, cudaStream_t);
+cudaError_t launch_agg_d32(const float *, const uint8_t *, int, const float *, int, int, int, float,
+                           float, int16_t *, float *, float *, cudaStream_t);
+cudaError_t launch_agg_d64(const float *, const uint8_t *, int, const float *, int, int, int, float,
+                           float, int16_t *, float *, float *, cudaStream_t);
+
+bool ncc_supported(int D, int ncc_r) {
+    return (D == 16 || D == 32 || D == 64) && ncc_r >= 1 && ncc_r <= 5;
+}
+bool agg_supported(int D, int agg_r) {
+    return (D == 16 || D == 32 || D == 64) && agg_r >= 1 && agg_r <= 7;
+}
+
+cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
+                       const float *mu_l, const float *inv_l, const float *mu_r,
+                       const float *inv_r, int W, int H, int D, int ncc_r, float *vol,
+                       cudaStream_t st) {
+    switch (D) {
+        case 16: return launch_ncc_d16(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st);
+        case 32: return launch_ncc_d32(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st);
+        case 64: return launch_ncc_d64(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_agg(const float *vol, const uint8_t *guide_u8, int pitch,
+                       const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
+                       float gamma_r, int16_t *lbl, float *dsub, float *agg, cudaStream_t st) {
+    const float log2e = 1.4426950408889634f;
+    const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
+    switch (D) {
+        case 16: return launch_agg_d16(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
+        case 32: return launch_agg_d32(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
+        case 64: return launch_agg_d64(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace sr
+
+namespace {
+
+constexpr int kStages = 7;
+const char *const kStageNames = "warp,stats,ncc_ref,ncc_tgt,agg_ref,agg_tgt,lrc_post";
+
+}  // namespace
+
+struct sr_ctx {
+    sr_params p{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    double alpha0 = 0, alpha1 = 0, delta = 0;
+    double f_px = 0, baseline = 0, u0 = 0, v0 = 0;
+    bool camera = false;
+    // scratch (owned)
+    float *rw = nullptr, *mu_l = nullptr, *inv_l = nullptr, *mu_r = nullptr, *inv_r = nullptr;
+    float *vol_l = nullptr, *vol_r = nullptr, *dsub = nullptr;
+    int16_t *lbl_l = nullptr, *lbl_r = nullptr;
+    float *agg_l = nullptr, *agg_r = nullptr;
+    uint8_t *stage_l = nullptr, *stage_r = nullptr;
+    float *stage_disp = nullptr;
+    int debug = 0;
+    bool matched = false, agg_valid = false;
+    bool profiling = false, timed = false;
+    cudaEvent_t ev[kStages + 1] = {};
+    char err[256] = {0};
+};
+
+namespace {
+
+sr_status fail_cuda(sr_ctx *c, cudaError_t e, const char *what) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+}
+
+#define SR_TRY(c, expr, what)                           \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return fail_cuda(c, e_, what); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+void free_all(sr_ctx *c) {
+    void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
+                    c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
+                    c->stage_disp};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
+
+}  // namespace
+
+extern "C" {
+
+const char *sr_version(void) { return "sr 0.1 (sm_103a, staged fp32)"; }
+
+const char *sr_status_str(sr_status s) {
+    switch (s) {
+        case SR_OK: return "SR_OK";
+        case SR_ERR_INVALID_ARG: return "SR_ERR_INVALID_ARG";
+        case SR_ERR_UNSUPPORTED: return "SR_ERR_UNSUPPORTED";
+        case SR_ERR_OOM: return "SR_ERR_OOM";
+        case SR_ERR_CUDA: return "SR_ERR_CUDA";
+        case SR_ERR_STATE: return "SR_ERR_STATE";
+        case SR_ERR_TIMEOUT: return "SR_ERR_TIMEOUT";
+    }
+    return "SR_ERR_UNKNOWN";
+}
+
+const char *sr_last_error(const sr_ctx *c) { return c ? c->err : ""; }
+
+const char *sr_stage_names(void) { return kStageNames; }
+
+int sr_kernels_per_match(const sr_ctx *c) {
+    (void)c;
+    return 8;   // warp, 2x stats, 2x ncc, 2x agg, lrc_post
+}
+
+sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
+    if (!out) return SR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params) return SR_ERR_INVALID_ARG;
+    const sr_params &p = *params;
+    if (p.width < 1 || p.height < 1 || p.width > 16384 || p.height > 16384 || p.max_disp < 1 ||
+        p.ncc_radius < 0 || p.agg_radius < 0 || !finite_pos(p.gamma_d) ||
+        !finite_pos(p.gamma_r) || !(p.lr_thresh >= 0.0f) || !isfinite(p.lr_thresh))
+        return SR_ERR_INVALID_ARG;
+    if (p.vol_dtype != SR_VOL_F32 && p.vol_dtype != SR_VOL_F16 && p.vol_dtype != SR_VOL_BF16)
+        return SR_ERR_INVALID_ARG;
+    if (!sr::ncc_supported(p.max_disp, p.ncc_radius) || !sr::agg_supported(p.max_disp, p.agg_radius) ||
+        p.vol_dtype != SR_VOL_F32)
+        return SR_ERR_UNSUPPORTED;
+
+    sr_ctx *c = new (std::nothrow) sr_ctx();
+    if (!c) return SR_ERR_OOM;
+    c->p = p;
+    c->st = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
+    const size_t W = p.width, H = p.height, D = p.max_disp, npx = W * H;
+    const size_t WE = W + D - 1;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(&c->rw, npx);
+    if (e == cudaSuccess) e = dalloc(&c->mu_l, H * WE);
+    if (e == cudaSuccess) e = dalloc(&c->mu_r, H * WE);
+    if (e == cudaSuccess) e = dalloc(&c->inv_l, H * WE);
+    if (e == cudaSuccess) e = dalloc(&c->inv_r, H * WE);
+    if (e == cudaSuccess) e = dalloc(&c->vol_l, npx * D);
+    if (e == cudaSuccess) e = dalloc(&c->vol_r, npx * D);
+    if (e == cudaSuccess) e = dalloc(&c->dsub, npx);
+    if (e == cudaSuccess) e = dalloc(&c->lbl_l, npx);
+    if (e == cudaSuccess) e = dalloc(&c->lbl_r, npx);
+    for (int i = 0; i <= kStages && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // clear a sticky allocation error
+        free_all(c);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+    }
+    *out = c;
+    return SR_OK;
+}
+
+sr_status sr_destroy(sr_ctx *c) {
+    if (!c) return SR_OK;
+    cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+    return SR_OK;
+}
+
+sr_status sr_set_plane(sr_ctx *c, double alpha0, double alpha1, double delta) {
+    if (!c || !isfinite(alpha0) || !isfinite(alpha1) || !isfinite(delta)) return SR_ERR_INVALID_ARG;
+    c->alpha0 = alpha0;
+    c->alpha1 = alpha1;
+    c->delta = delta;
+    return SR_OK;
+}
+
+sr_status sr_set_camera(sr_ctx *c, double f_px, double baseline, double u0, double v0) {
+    if (!c || !(f_px > 0) || !isfinite(f_px) || !(baseline > 0) || !isfinite(baseline) ||
+        !isfinite(u0) || !isfinite(v0))
+        return SR_ERR_INVALID_ARG;
+    c->f_px = f_px;
+    c->baseline = baseline;
+    c->u0 = u0;
+    c->v0 = v0;
+    c->camera = true;
+    return SR_OK;
+}
+
+sr_status sr_set_debug(sr_ctx *c, int flags) {
+    if (!c || (flags & ~SR_DEBUG_KEEP_AGG)) return SR_ERR_INVALID_ARG;
+    if ((flags & SR_DEBUG_KEEP_AGG) && !c->agg_l) {
+        const size_t n = (size_t)c->p.width * c->p.height * c->p.max_disp;
+        SR_TRY(c, dalloc(&c->agg_l, n), "cudaMalloc(agg_l)");
+        SR_TRY(c, dalloc(&c->agg_r, n), "cudaMalloc(agg_r)");
+    }
+    c->debug = flags;
+    return SR_OK;
+}
+
+sr_status sr_set_profiling(sr_ctx *c, int enable) {
+    if (!c) return SR_ERR_INVALID_ARG;
+    c->profiling = enable != 0;
+    c->timed = false;
+    return SR_OK;
+}
+
+sr_status sr_stage_times(sr_ctx *c, float *ms, int n, int *count) {
+    if (!c || (n > 0 && !ms)) return SR_ERR_INVALID_ARG;
+    if (count) *count = kStages;
+    if (!c->timed) return SR_ERR_STATE;
+    SR_TRY(c, cudaEventSynchronize(c->ev[kStages]), "cudaEventSynchronize");
+    for (int i = 0; i < kStages && i < n; ++i)
+        SR_TRY(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime");
+    return SR_OK;
+}
+
+sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
+                   float *d_disp, int16_t *d_wta_or_null) {
+    if (!c || !d_left || !d_right || !d_disp || pitch_bytes < c->p.width) return SR_ERR_INVALID_ARG;
+    const sr_params &p = c->p;
+    const int W = p.width, H = p.height, D = p.max_disp;
+    cudaStream_t st = c->st;
+    const bool prof = c->profiling;
+    const bool keep = (c->debug & SR_DEBUG_KEEP_AGG) != 0;
+    int stage = 0;
+    auto mark = [&]() -> cudaError_t {
+        return prof ? cudaEventRecord(c->ev[stage++], st) : cudaSuccess;
+    };
+    c->matched = false;
+    c->timed = false;
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_warp(d_right, pitch_bytes, W, H, c->alpha0, c->alpha1, c->delta, c->rw, st),
+           "warp");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
+                               c->mu_r, c->inv_r, st),
+           "stats");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, st),
+           "ncc_ref");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_ncc(true, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, st),
+           "ncc_tgt");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_agg(c->vol_l, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
+                             p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
+                             st),
+           "agg_ref");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_agg(c->vol_r, nullptr, 0, c->rw, W, H, D, p.agg_radius, p.gamma_d,
+                             p.gamma_r, c->lbl_r, nullptr, keep ? c->agg_r : nullptr, st),
+           "agg_tgt");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->alpha0, c->alpha1,
+                                  c->delta, p.lr_thresh, d_disp, d_wta_or_null, st),
+           "lrc_post");
+    SR_TRY(c, mark(), "cudaEventRecord");
+    c->matched = true;
+    c->agg_valid = keep;
+    c->timed = prof;
+    return SR_OK;
+}
+
+sr_status sr_match_host(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right, float *h_disp) {
+    if (!c || !h_left || !h_right || !h_disp) return SR_ERR_INVALID_ARG;
+    const size_t npx = (size_t)c->p.width * c->p.height;
+    if (!c->stage_l) {
+        SR_TRY(c, dalloc(&c->stage_l, npx), "cudaMalloc(stage)");
+        SR_TRY(c, dalloc(&c->stage_r, npx), "cudaMalloc(stage)");
+        SR_TRY(c, dalloc(&c->stage_disp, npx), "cudaMalloc(stage)");
+    }
+    SR_TRY(c, cudaMemcpyAsync(c->stage_l, h_left, npx, cudaMemcpyHostToDevice, c->st), "H2D left");
+    SR_TRY(c, cudaMemcpyAsync(c->stage_r, h_right, npx, cudaMemcpyHostToDevice, c->st), "H2D right");
+    sr_status s = sr_match(c, c->stage_l, c->stage_r, c->p.width, c->stage_disp, nullptr);
+    if (s != SR_OK) return s;
+    SR_TRY(c, cudaMemcpyAsync(h_disp, c->stage_disp, npx * sizeof(float), cudaMemcpyDeviceToHost,
+                              c->st),
+           "D2H disp");
+    SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+    return SR_OK;
+}
+
+sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {
+    if (!c || !d_disp || !d_xyz) return SR_ERR_INVALID_ARG;
+    if (!c->camera) return SR_ERR_STATE;
+    SR_TRY(c, sr::launch_xyz(d_disp, c->p.width, c->p.height, c->f_px, c->baseline, c->u0, c->v0,
+                             d_xyz, c->st),
+           "xyz");
+    return SR_OK;
+}
+
+sr_status sr_get_buffer(sr_ctx *c, sr_buffer which, void *dst, size_t *bytes_inout) {
+    if (!c || !dst || !bytes_inout) return SR_ERR_INVALID_ARG;
+    const size_t npx = (size_t)c->p.width * c->p.height, D = c->p.max_disp;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (which) {
+        case SR_BUF_WARPED: src = c->rw; bytes = npx * 4; break;
+        case SR_BUF_MU_L: case SR_BUF_MU_R: case SR_BUF_INV_L: case SR_BUF_INV_R: {
+            // stored with D-1 extra block centres per row; copy the in-image ones
+            if (*bytes_inout < npx * 4) { *bytes_inout = npx * 4; return SR_ERR_INVALID_ARG; }
+            if (!c->matched) return SR_ERR_STATE;
+            const size_t WE = c->p.width + D - 1;
+            const float *base = which == SR_BUF_INV_L ? c->inv_l
+                              : which == SR_BUF_MU_L  ? c->mu_l
+                              : which == SR_BUF_INV_R ? c->inv_r + (D - 1)
+                                                      : c->mu_r + (D - 1);
+            SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+            SR_TRY(c, cudaMemcpy2D(dst, c->p.width * 4, base, WE * 4, c->p.width * 4, c->p.height,
+                                   cudaMemcpyDefault),
+                   "cudaMemcpy2D");
+            *bytes_inout = npx * 4;
+            return SR_OK;
+        }
+        case SR_BUF_COST_L: src = c->vol_l; bytes = npx * D * 4; break;
+        case SR_BUF_COST_R: src = c->vol_r; bytes = npx * D * 4; break;
+        case SR_BUF_AGG_L: src = c->agg_valid ? c->agg_l : nullptr; bytes = npx * D * 4; break;
+        case SR_BUF_AGG_R: src = c->agg_valid ? c->agg_r : nullptr; bytes = npx * D * 4; break;
+        case SR_BUF_WTA_L: src = c->lbl_l; bytes = npx * 2; break;
+        case SR_BUF_WTA_R: src = c->lbl_r; bytes = npx * 2; break;
+        case SR_BUF_DSUB: src = c->dsub; bytes = npx * 4; break;
+        default: return SR_ERR_INVALID_ARG;
+    }
+    if (*bytes_inout < bytes) { *bytes_inout = bytes; return SR_ERR_INVALID_ARG; }
+    if (!c->matched || !src) return SR_ERR_STATE;
+    SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+    SR_TRY(c, cudaMemcpy(dst, src, bytes, cudaMemcpyDefault), "cudaMemcpy");
+    *bytes_inout = bytes;
+    return SR_OK;
+}
+
+}  // extern "C"

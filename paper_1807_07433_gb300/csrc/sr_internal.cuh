@@ -1,0 +1,65 @@
+// sr_internal.cuh -- launchers shared by the kernel translation units and the
+// C ABI layer (sr_api.cu).  Not installed; the public interface is sr.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sr {
+
+// Offset subtracted from the sliding block in the NCC dot product.  Any
+// constant leaves Eq. 3 unchanged (the fixed block is centred, so the sum of
+// its centred values is zero); 128 keeps the products small for 0..255 data.
+constexpr float kNccOffset = 128.0f;
+
+// Variance below which a block counts as flat (NCC = 0).
+constexpr float kFlatVar = 1e-6f;
+
+// Supported compile-time parameter sets.
+bool ncc_supported(int D, int ncc_r);
+bool agg_supported(int D, int agg_r);
+
+// Sec. II-A perspective transformation: rw[v][x] = i_r(x - s(v), v),
+// s(v) = alpha0 + alpha1*v - delta, linear in x, clamp-to-edge.
+cudaError_t launch_warp(const uint8_t *right, int pitch, int W, int H, double alpha0,
+                        double alpha1, double delta, float *rw, cudaStream_t st);
+
+// Eqs. 4-5 block statistics, for block centres on an extended range (the
+// sliding block of the target volume is centred up to u+D-1, that of the
+// reference volume down to u-(D-1)).  mu_l, inv_l: [H][W+D-1] for centres x in
+// [0, W+D-1); mu_r, inv_r: [H][W+D-1] for centres x in [-(D-1), W) stored at
+// x+D-1.  inv = 1/(n*sigma), 0 for a flat block.
+cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W, int H, int D,
+                         int ncc_r, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
+                         cudaStream_t st);
+
+// Eq. 3 cost volume [H][W][D] (float).  target = false: reference volume
+// c(u,v,d) = NCC(left block u, warped-target block u-d); target = true:
+// target volume c(u,v,d) = NCC(left block u+d, warped-target block u).
+cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
+                       const float *mu_l, const float *inv_l, const float *mu_r,
+                       const float *inv_r, int W, int H, int D, int ncc_r, float *vol,
+                       cudaStream_t st);
+
+// Eqs. 8-10 bilateral aggregation fused with WTA (Sec. II-B-3) and, for the
+// reference view, the Eq. 12 parabola.  Guide: the left image (uint8, when
+// guide_u8 != nullptr) or the warped target (float).  Writes lbl [H][W]
+// int16, dsub [H][W] float (nullable) and, for inspection, the normalised
+// aggregated volume agg [H][W][D] (nullable).
+cudaError_t launch_agg(const float *vol, const uint8_t *guide_u8, int pitch,
+                       const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
+                       float gamma_r, int16_t *lbl, float *dsub, float *agg, cudaStream_t st);
+
+// Eq. 11 check with tolerance, then Sec. II-C post-processing.
+cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,
+                            int H, double alpha0, double alpha1, double delta, float lr_thresh,
+                            float *disp, int16_t *wta_out, cudaStream_t st);
+
+// Sec. II-D reconstruction, three planes X, Y, Z of [H][W].
+cudaError_t launch_xyz(const float *disp, int W, int H, double f_px, double baseline, double u0,
+                       double v0, float *xyz, cudaStream_t st);
+
+__host__ __device__ inline int clampi(int x, int lo, int hi) {
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+}  // namespace sr

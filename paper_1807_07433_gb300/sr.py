@@ -1,0 +1,271 @@
+"""Python binding of the C ABI in include/sr.h (ctypes; argument marshalling only).
+
+Every function keeps the C name and order of arguments.  Device buffers are
+passed as torch CUDA tensors (or raw integer device pointers); all arithmetic
+runs in libsr.so's CUDA kernels.  If libsr.so is missing this module raises on
+first use -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsr.so")
+
+SR_OK, SR_ERR_INVALID_ARG, SR_ERR_UNSUPPORTED, SR_ERR_OOM, SR_ERR_CUDA, SR_ERR_STATE, \
+    SR_ERR_TIMEOUT = range(7)
+SR_VOL_F32, SR_VOL_F16, SR_VOL_BF16 = range(3)
+(SR_BUF_WARPED, SR_BUF_MU_L, SR_BUF_INV_L, SR_BUF_MU_R, SR_BUF_INV_R, SR_BUF_COST_L,
+ SR_BUF_COST_R, SR_BUF_AGG_L, SR_BUF_AGG_R, SR_BUF_WTA_L, SR_BUF_WTA_R, SR_BUF_DSUB) = range(12)
+SR_DEBUG_KEEP_AGG = 1
+
+# Functions the header declares (tests check the library exports each one).
+EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
+           "sr_match_host", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
+           "sr_set_profiling", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
+           "sr_status_str", "sr_last_error", "sr_version")
+
+
+class sr_params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("max_disp", ctypes.c_int),
+                ("ncc_radius", ctypes.c_int), ("agg_radius", ctypes.c_int),
+                ("gamma_d", ctypes.c_float), ("gamma_r", ctypes.c_float),
+                ("lr_thresh", ctypes.c_float), ("vol_dtype", ctypes.c_int)]
+
+
+class SrError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {status_name(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libsr.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise OSError(f"{p} not found: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(p)
+            vp, i, d, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float
+            sz = ctypes.c_size_t
+            sigs = {
+                "sr_create": (i, [ctypes.POINTER(sr_params), vp, ctypes.POINTER(vp)]),
+                "sr_destroy": (i, [vp]),
+                "sr_set_plane": (i, [vp, d, d, d]),
+                "sr_set_camera": (i, [vp, d, d, d, d]),
+                "sr_match": (i, [vp, vp, vp, i, vp, vp]),
+                "sr_match_host": (i, [vp, vp, vp, vp]),
+                "sr_reconstruct": (i, [vp, vp, vp]),
+                "sr_get_buffer": (i, [vp, i, vp, ctypes.POINTER(sz)]),
+                "sr_set_debug": (i, [vp, i]),
+                "sr_set_profiling": (i, [vp, i]),
+                "sr_stage_times": (i, [vp, ctypes.POINTER(f), i, ctypes.POINTER(i)]),
+                "sr_stage_names": (ctypes.c_char_p, []),
+                "sr_kernels_per_match": (i, [vp]),
+                "sr_status_str": (ctypes.c_char_p, [i]),
+                "sr_last_error": (ctypes.c_char_p, [vp]),
+                "sr_version": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_name(s: int) -> str:
+    try:
+        return load().sr_status_str(int(s)).decode()
+    except OSError:
+        return f"status {s}"
+
+
+def _ptr(x) -> int | None:
+    """Device/host address of a torch tensor, numpy array or raw int (None = NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _check(ctx, status: int, where: str):
+    if status != SR_OK:
+        detail = load().sr_last_error(ctx).decode() if ctx else ""
+        raise SrError(status, where, detail)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(width, height, max_disp, ncc_radius, agg_radius, gamma_d, gamma_r,
+                lr_thresh=1.0, vol_dtype=SR_VOL_F32) -> sr_params:
+    return sr_params(int(width), int(height), int(max_disp), int(ncc_radius), int(agg_radius),
+                     float(gamma_d), float(gamma_r), float(lr_thresh), int(vol_dtype))
+
+
+def sr_create(params: sr_params, cuda_stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(None, load().sr_create(ctypes.byref(params), _stream_handle(cuda_stream),
+                                  ctypes.byref(ctx)), "sr_create")
+    return ctx
+
+
+def sr_destroy(ctx) -> None:
+    _check(None, load().sr_destroy(ctx), "sr_destroy")
+
+
+def sr_set_plane(ctx, alpha0: float, alpha1: float, delta: float) -> None:
+    _check(ctx, load().sr_set_plane(ctx, alpha0, alpha1, delta), "sr_set_plane")
+
+
+def sr_set_camera(ctx, f_px: float, baseline: float, u0: float, v0: float) -> None:
+    _check(ctx, load().sr_set_camera(ctx, f_px, baseline, u0, v0), "sr_set_camera")
+
+
+def sr_match(ctx, d_left, d_right, pitch_bytes: int, d_disp, d_wta_or_null=None) -> None:
+    _check(ctx, load().sr_match(ctx, _ptr(d_left), _ptr(d_right), int(pitch_bytes),
+                                _ptr(d_disp), _ptr(d_wta_or_null)), "sr_match")
+
+
+def sr_match_host(ctx, h_left, h_right, h_disp) -> None:
+    _check(ctx, load().sr_match_host(ctx, _ptr(h_left), _ptr(h_right), _ptr(h_disp)),
+           "sr_match_host")
+
+
+def sr_reconstruct(ctx, d_disp, d_xyz) -> None:
+    _check(ctx, load().sr_reconstruct(ctx, _ptr(d_disp), _ptr(d_xyz)), "sr_reconstruct")
+
+
+def sr_get_buffer(ctx, which: int, dst, nbytes: int) -> int:
+    n = ctypes.c_size_t(nbytes)
+    _check(ctx, load().sr_get_buffer(ctx, int(which), _ptr(dst), ctypes.byref(n)),
+           "sr_get_buffer")
+    return n.value
+
+
+def sr_set_debug(ctx, flags: int) -> None:
+    _check(ctx, load().sr_set_debug(ctx, int(flags)), "sr_set_debug")
+
+
+def sr_set_profiling(ctx, enable: bool) -> None:
+    _check(ctx, load().sr_set_profiling(ctx, int(bool(enable))), "sr_set_profiling")
+
+
+def sr_stage_times(ctx) -> dict:
+    n = 16
+    arr = (ctypes.c_float * n)()
+    cnt = ctypes.c_int()
+    _check(ctx, load().sr_stage_times(ctx, arr, n, ctypes.byref(cnt)), "sr_stage_times")
+    names = sr_stage_names()
+    return {names[k]: float(arr[k]) for k in range(cnt.value)}
+
+
+def sr_stage_names() -> list[str]:
+    return load().sr_stage_names().decode().split(",")
+
+
+def sr_kernels_per_match(ctx) -> int:
+    return int(load().sr_kernels_per_match(ctx))
+
+
+def sr_version() -> str:
+    return load().sr_version().decode()
+
+
+# ------------------------------------------------------------ convenience layer
+
+_BUF_SPEC = {  # which -> (dtype, per-pixel shape suffix uses D?)
+    SR_BUF_WARPED: (np.float32, False), SR_BUF_MU_L: (np.float32, False),
+    SR_BUF_INV_L: (np.float32, False), SR_BUF_MU_R: (np.float32, False),
+    SR_BUF_INV_R: (np.float32, False), SR_BUF_COST_L: (np.float32, True),
+    SR_BUF_COST_R: (np.float32, True), SR_BUF_AGG_L: (np.float32, True),
+    SR_BUF_AGG_R: (np.float32, True), SR_BUF_WTA_L: (np.int16, False),
+    SR_BUF_WTA_R: (np.int16, False), SR_BUF_DSUB: (np.float32, False),
+}
+
+
+class Matcher:
+    """A context plus the calls a user makes, on torch tensors.
+
+    >>> m = Matcher(W, H, D, ncc_radius, agg_radius, gamma_d, gamma_r)
+    >>> m.set_plane(alpha0, alpha1, delta)
+    >>> disp = m.match(left_u8_cuda, right_u8_cuda)       # float32 [H, W], NaN = rejected
+    """
+
+    def __init__(self, width, height, max_disp, ncc_radius, agg_radius, gamma_d, gamma_r,
+                 lr_thresh=1.0, vol_dtype=SR_VOL_F32, stream=None):
+        self.params = make_params(width, height, max_disp, ncc_radius, agg_radius, gamma_d,
+                                  gamma_r, lr_thresh, vol_dtype)
+        self.W, self.H, self.D = int(width), int(height), int(max_disp)
+        self.ctx = sr_create(self.params, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            sr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_plane(self, alpha0, alpha1, delta):
+        sr_set_plane(self.ctx, alpha0, alpha1, delta)
+
+    def set_camera(self, f_px, baseline, u0=None, v0=None):
+        u0 = (self.W - 1) / 2.0 if u0 is None else u0
+        v0 = (self.H - 1) / 2.0 if v0 is None else v0
+        sr_set_camera(self.ctx, f_px, baseline, u0, v0)
+
+    def match(self, left, right, disp=None, wta=None):
+        import torch
+        if disp is None:
+            disp = torch.empty((self.H, self.W), dtype=torch.float32, device=left.device)
+        pitch = left.stride(0) * left.element_size()
+        assert right.stride(0) == left.stride(0), "left and right must share a pitch"
+        sr_match(self.ctx, left, right, pitch, disp, wta)
+        return disp
+
+    def reconstruct(self, disp, xyz=None):
+        import torch
+        if xyz is None:
+            xyz = torch.empty((3, self.H, self.W), dtype=torch.float32, device=disp.device)
+        sr_reconstruct(self.ctx, disp, xyz)
+        return xyz
+
+    def buffer(self, which: int) -> np.ndarray:
+        dt, vol = _BUF_SPEC[which]
+        shape = (self.H, self.W, self.D) if vol else (self.H, self.W)
+        out = np.empty(shape, dt)
+        sr_get_buffer(self.ctx, which, out, out.nbytes)
+        return out

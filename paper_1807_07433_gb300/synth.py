@@ -145,6 +145,8 @@ def make_pair(sc: Scene):
     d_true = disp(u)
     tex_l = _texture(tables, u, v)
     m, s = tex_l.mean(), tex_l.std()
+    if not s > 0.0:          # a single pixel has no spread
+        s = 1.0
     scale = lambda t: 128.0 + 40.0 * (t - m) / s  # noqa: E731
 
     ul = u + plane

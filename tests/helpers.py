@@ -1,0 +1,83 @@
+"""Shared helpers for the parity tests: run the CUDA path through the C ABI and
+the FP64 oracle on the same seeded inputs, and compare them with the stated
+tolerances.
+
+Tolerances (derivation in the design notes; FP32 unit roundoff u = 2^-24):
+  TOL_WARP   1e-4  warped intensities (<= 255, two FP32 ops: ~3e-5)
+  TOL_MU     1e-4  block means (<= 255, n <= 121 FP32 adds)
+  TOL_SIG    1e-5  relative error of 1/(n sigma)
+  TOL_COST   1e-4  NCC cost in [-1, 1] (centred FP32 dot product; the bound
+                   grows like n*u*sum|a||s|/(n sigma_f sigma_s), largest on
+                   near-flat blocks)
+  TOL_AGG    2e-5  aggregated cost (weighted mean of costs, FP32 weights)
+  TAU_TIE    1e-4  a WTA label may differ only where the oracle's best and
+                   second-best aggregated costs are closer than this
+  TOL_DSUB   1e-3  px, subpixel disparity away from near-ties: where labels
+                   agree, the oracle's top-2 gap is >= TAU_TIE and its parabola
+                   denominator |den| >= DEN_MIN.  The Eq. 12 offset moves by
+                   about 6 eps / |den| for a cost error eps; FP32 storage of
+                   the warped image alone gives eps ~ 1e-6 on low-texture
+                   blocks, so |den| < 6e-3 is an ill-conditioned (near-tie)
+                   parabola.
+  DEN_MIN    6e-3
+  AGREE_MIN  0.999 fraction of integer disparities that must agree
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TOL_WARP = 1e-4
+TOL_MU = 1e-4
+TOL_SIG = 1e-5
+TOL_COST = 1e-4
+TOL_AGG = 2e-5
+TAU_TIE = 1e-4
+TOL_DSUB = 1e-3
+DEN_MIN = 6e-3
+AGREE_MIN = 0.999
+
+
+def oracle_params(w):
+    import oracle
+    return oracle.Params(W=w.scene.W, H=w.scene.H, D=w.D, ncc_r=w.ncc_r, agg_r=w.agg_r,
+                         gamma_d=w.gamma_d, gamma_r=w.gamma_r, lr_thresh=w.lr_thresh,
+                         alpha0=w.scene.alpha0, alpha1=w.scene.alpha1, delta=w.delta,
+                         f_px=w.f_px, baseline=w.baseline_mm)
+
+
+def run_gpu(w, left, right, keep_agg=False, buffers=()):
+    """Run sr_match (+ sr_reconstruct) on cuda:0 through the C ABI; return numpy arrays."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    H, W = left.shape
+    dl = torch.from_numpy(left).cuda()
+    dr = torch.from_numpy(right).cuda()
+    out = {}
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        m.set_camera(w.f_px, w.baseline_mm)
+        if keep_agg:
+            sr.sr_set_debug(m.ctx, sr.SR_DEBUG_KEEP_AGG)
+        wta = torch.empty((H, W), dtype=torch.int16, device="cuda")
+        disp = m.match(dl, dr, wta=wta)
+        xyz = m.reconstruct(disp)
+        torch.cuda.synchronize()
+        out["dfull"] = disp.cpu().numpy()
+        out["wta"] = wta.cpu().numpy()
+        out["xyz"] = xyz.cpu().numpy()
+        for name, which in buffers:
+            out[name] = m.buffer(which)
+    return out
+
+
+def run_oracle(w, left, right, want):
+    import oracle
+    return oracle.match(oracle_params(w), left, right, want=want)
+
+
+def label_report(gpu_lbl, orc_lbl, orc_gap):
+    """Return (agree fraction, mismatches that are not near-ties)."""
+    diff = gpu_lbl.astype(np.int64) != orc_lbl.astype(np.int64)
+    bad = diff & ~(orc_gap < TAU_TIE)
+    return 1.0 - diff.mean(), int(bad.sum())

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Small workloads (the oracle finishes in seconds; several tiles plus ragged
+tails) are compared stage by stage and element by element.  The full
+1280x720x64 workload is compared on sampled pixels, which the oracle
+evaluates one by one, plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+from helpers import (AGREE_MIN, DEN_MIN, TAU_TIE, TOL_AGG, TOL_COST, TOL_DSUB, TOL_MU, TOL_SIG,
+                     TOL_WARP, label_report, oracle_params, run_gpu, run_oracle)
+from paper_1807_07433_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ALL = ("warped", "mu_l", "sig_l", "mu_r", "sig_r", "cost_l", "cost_r", "agg_l", "agg_r",
+       "lbl_l", "lbl_r", "gap_l", "gap_r", "den_l", "dsub", "valid", "dfull", "xyz")
+
+
+def _buffers():
+    from paper_1807_07433_gb300 import sr
+    return (("warped", sr.SR_BUF_WARPED), ("mu_l", sr.SR_BUF_MU_L), ("inv_l", sr.SR_BUF_INV_L),
+            ("mu_r", sr.SR_BUF_MU_R), ("inv_r", sr.SR_BUF_INV_R), ("cost_l", sr.SR_BUF_COST_L),
+            ("cost_r", sr.SR_BUF_COST_R), ("agg_l", sr.SR_BUF_AGG_L), ("agg_r", sr.SR_BUF_AGG_R),
+            ("lbl_l", sr.SR_BUF_WTA_L), ("lbl_r", sr.SR_BUF_WTA_R), ("dsub", sr.SR_BUF_DSUB))
+
+
+CASES = [
+    synth.C1,                                                    # 160x120 D16 ncc5 bil9
+    synth.small(203, 77, D=32, ncc_r=3, agg_r=5, seed=11),       # ragged, several tiles
+    synth.small(97, 45, D=64, ncc_r=1, agg_r=7, seed=12, gamma_d=5.0, gamma_r=15.0),
+    synth.small(70, 38, D=64, ncc_r=5, agg_r=2, seed=13, alpha1=0.11),
+    synth.small(33, 5, D=16, ncc_r=2, agg_r=3, seed=14),         # fewer rows than the window
+    synth.small(1, 1, D=16, ncc_r=1, agg_r=1, seed=15),          # degenerate 1x1
+    synth.small(5, 2, D=16, ncc_r=3, agg_r=4, seed=16),
+]
+
+
+def _n_nonflat(sig):
+    return sig > 1e-3
+
+
+@pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
+def test_stagewise_parity(w):
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right, keep_agg=True, buffers=_buffers())
+    o = run_oracle(w, left, right, ALL)
+    n = (2 * w.ncc_r + 1) ** 2
+
+    np.testing.assert_allclose(g["warped"], o.warped, rtol=0, atol=TOL_WARP)
+    np.testing.assert_allclose(g["mu_l"], o.mu_l, rtol=0, atol=TOL_MU)
+    np.testing.assert_allclose(g["mu_r"], o.mu_r, rtol=0, atol=TOL_MU)
+    for side in ("l", "r"):
+        sig = getattr(o, "sig_" + side)
+        inv = g["inv_" + side]
+        ok = _n_nonflat(sig)
+        np.testing.assert_allclose(inv[ok] * n * sig[ok], 1.0, rtol=0, atol=TOL_SIG)
+        assert np.all(inv[sig ** 2 < 1e-7] == 0.0)
+
+    np.testing.assert_allclose(g["cost_l"], o.cost_l, rtol=0, atol=TOL_COST)
+    np.testing.assert_allclose(g["cost_r"], o.cost_r, rtol=0, atol=TOL_COST)
+    np.testing.assert_allclose(g["agg_l"], o.agg_l, rtol=0, atol=TOL_AGG)
+    np.testing.assert_allclose(g["agg_r"], o.agg_r, rtol=0, atol=TOL_AGG)
+
+    agree_l, bad_l = label_report(g["lbl_l"], o.lbl_l, o.gap_l)
+    agree_r, bad_r = label_report(g["lbl_r"], o.lbl_r, o.gap_r)
+    assert bad_l == 0 and bad_r == 0
+    assert agree_l >= AGREE_MIN and agree_r >= AGREE_MIN
+    np.testing.assert_array_equal(g["wta"], g["lbl_l"])
+
+    same = (g["lbl_l"] == o.lbl_l)
+    sharp = same & (np.abs(o.den_l) >= DEN_MIN) & (o.gap_l >= TAU_TIE)
+    np.testing.assert_allclose(g["dsub"][sharp], o.dsub[sharp], rtol=0, atol=TOL_DSUB)
+    ends = same & (o.den_l == 0.0)
+    np.testing.assert_array_equal(g["dsub"][ends], o.dsub[ends])
+
+    # L-R validity and the post-processed map: where both label maps agree at
+    # the pixel and at its match, validity is identical and d agrees.
+    H, W = left.shape
+    uu = np.arange(W)[None, :] - o.lbl_l
+    inb = uu >= 0
+    match_same = np.zeros_like(same)
+    vv = np.broadcast_to(np.arange(H)[:, None], (H, W))
+    match_same[inb] = g["lbl_r"][vv[inb], uu[inb]] == o.lbl_r[vv[inb], uu[inb]]
+    firm = same & (match_same | ~inb)
+    gv = np.isfinite(g["dfull"])
+    np.testing.assert_array_equal(gv[firm], o.valid.astype(bool)[firm])
+    both = firm & gv & (np.abs(o.den_l) >= DEN_MIN) & (o.gap_l >= TAU_TIE)
+    np.testing.assert_allclose(g["dfull"][both], o.dfull[both], rtol=0, atol=TOL_DSUB)
+
+
+@pytest.mark.parametrize("w", CASES[:3], ids=lambda w: w.name)
+def test_reconstruct_matches_closed_form(w):
+    import oracle
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right)
+    p = oracle_params(w)
+    H, W = left.shape
+    want = np.full((3, H, W), np.nan)
+    for v in range(H):
+        for u in range(W):
+            want[:, v, u] = oracle.reconstruct(p, float(g["dfull"][v, u]), u, v)
+    fin = np.isfinite(want)
+    np.testing.assert_array_equal(np.isfinite(g["xyz"]), fin)
+    np.testing.assert_allclose(g["xyz"][fin], want[fin], rtol=2e-6, atol=1e-3)
+
+
+def test_two_volume_identity_on_gpu():
+    """Sec. II-B-1: the target volume at (u-d,v,d) equals the reference volume
+    at (u,v,d); the GPU computes the two independently."""
+    from paper_1807_07433_gb300 import sr
+    w = CASES[1]
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right, buffers=(("cost_l", sr.SR_BUF_COST_L),
+                                         ("cost_r", sr.SR_BUF_COST_R)))
+    W = left.shape[1]
+    for d in range(w.D):
+        np.testing.assert_allclose(g["cost_r"][:, :W - d, d], g["cost_l"][:, d:, d], rtol=0,
+                                   atol=2 * TOL_COST)
+    assert np.abs(g["cost_l"]).max() <= 1.0 + 1e-5
+
+
+def test_full_size_sampled_pixels():
+    """The 1280x720x64 workload in the benchmark's launch configuration,
+    checked at sampled pixels that the oracle evaluates one by one."""
+    import oracle
+    w = synth.C2
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right)
+    H, W = left.shape
+    rng = np.random.default_rng(2024)
+    us = np.concatenate([rng.integers(0, W, 150), [0, W - 1, 0, W - 1, 5, W - 6, 640, 641]])
+    vs = np.concatenate([rng.integers(0, H, 150), [0, 0, H - 1, H - 1, 3, H - 4, 360, 360]])
+    o = oracle.match_pixels(oracle_params(w), left, right, us, vs)
+    gl = g["wta"][vs, us]
+    diff = gl != o["lbl_l"]
+    assert np.all(o["gap_l"][diff] < TAU_TIE)
+    assert diff.mean() <= 1.0 - AGREE_MIN + 1.0 / len(us)
+    sharp = ~diff & (np.abs(o["den_l"]) >= DEN_MIN) & (o["gap_l"] >= TAU_TIE) & \
+        np.isfinite(o["dfull"]) & np.isfinite(g["dfull"][vs, us])
+    np.testing.assert_allclose(g["dfull"][vs, us][sharp], o["dfull"][sharp], rtol=0,
+                               atol=TOL_DSUB)
+    firm = ~diff & (o["gap_r_match"] >= TAU_TIE)
+    np.testing.assert_array_equal(np.isfinite(g["dfull"][vs, us])[firm],
+                                  o["valid"].astype(bool)[firm])
+    # properties at full size
+    fin = np.isfinite(g["dfull"])
+    assert fin.mean() > 0.8
+    assert np.all(g["wta"] >= 0) and np.all(g["wta"] < w.D)
+
+
+def test_match_host_equals_device_path():
+    import torch
+    from paper_1807_07433_gb300 import sr
+    w = CASES[1]
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    g = run_gpu(w, left, right)
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        hl = torch.from_numpy(left).pin_memory()
+        hr = torch.from_numpy(right).pin_memory()
+        hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        sr.sr_match_host(m.ctx, hl, hr, hd)
+        np.testing.assert_array_equal(np.isnan(hd.numpy()), np.isnan(g["dfull"]))
+        fin = np.isfinite(g["dfull"])
+        np.testing.assert_array_equal(hd.numpy()[fin], g["dfull"][fin])
+
+
+def test_repeatable():
+    """Same inputs give bit-identical outputs (no atomics or races in the path)."""
+    w = CASES[0]
+    left, right, _ = synth.make_pair(w.scene)
+    a = run_gpu(w, left, right)
+    b = run_gpu(w, left, right)
+    np.testing.assert_array_equal(a["wta"], b["wta"])
+    np.testing.assert_array_equal(np.nan_to_num(a["dfull"], nan=-1), np.nan_to_num(b["dfull"], nan=-1))
+
+
+def test_stage_timing_and_launch_count():
+    import torch
+    from paper_1807_07433_gb300 import sr
+    w = CASES[0]
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        sr.sr_set_profiling(m.ctx, True)
+        m.match(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda())
+        t = sr.sr_stage_times(m.ctx)
+        assert list(t) == sr.sr_stage_names()
+        assert all(v >= 0.0 for v in t.values())
+        assert sr.sr_kernels_per_match(m.ctx) == 8
+
+
+def test_error_paths_on_device():
+    import torch
+    from paper_1807_07433_gb300 import sr
+    with sr.Matcher(64, 32, 16, 2, 2, 3.0, 10.0) as m:
+        left = torch.zeros((32, 64), dtype=torch.uint8, device="cuda")
+        with pytest.raises(sr.SrError) as e:
+            sr.sr_match(m.ctx, left, left, 63, torch.empty((32, 64), device="cuda"))
+        assert e.value.status == sr.SR_ERR_INVALID_ARG
+        with pytest.raises(sr.SrError) as e:
+            sr.sr_reconstruct(m.ctx, torch.empty((32, 64), device="cuda"),
+                              torch.empty((3, 32, 64), device="cuda"))
+        assert e.value.status == sr.SR_ERR_STATE
+        with pytest.raises(sr.SrError) as e:
+            m.buffer(sr.SR_BUF_AGG_L)
+        assert e.value.status == sr.SR_ERR_STATE
+        # flat images: every block is flat, every cost 0, all labels 0
+        m.match(left, left)
+        torch.cuda.synchronize()
+        assert int(m.buffer(sr.SR_BUF_WTA_L).max()) == 0
+        assert np.all(m.buffer(sr.SR_BUF_COST_L) == 0.0)
