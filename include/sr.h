@@ -125,6 +125,33 @@ sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, i
 sr_status sr_match_host(sr_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                         float *h_disp);
 
+/* sr_match for callers that cannot allocate device memory.  (The paper has
+ * no counterpart: this entry point concerns only memory ownership.)
+ * Some callers cannot call cudaMalloc -- a host that fixes the library's
+ * device-memory budget at start-up and forbids allocation afterwards, a
+ * plug-in whose host owns the device allocator, a real-time loop that must
+ * never wait on the allocator.  This call needs no context and allocates
+ * nothing: the intermediates of the match live in one fixed device array of
+ * 32 MiB inside libsr.so, which every GPU that loads the library holds until
+ * the process exits.  Inputs, outputs and parameters have the meaning they
+ * have for sr_create + sr_set_plane + sr_match; d_disp receives the same
+ * values sr_match writes.
+ *   Size limit: with A(b) = b rounded up to a multiple of 256,
+ *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + 2*A(4*W*H*D) + 2*A(2*W*H) <= 32 MiB
+ *   (e.g. 480x360 at D = 16, 320x180 at D = 64); larger frames are rejected
+ *   with SR_ERR_UNSUPPORTED before any GPU work.
+ *   The first call on a device looks up the array's device address with
+ *   cudaGetSymbolAddress (with that device current); make that first call
+ *   before any stream capture.
+ *   Every call reuses the same array and leaves its contents behind; nothing
+ *   in it needs to start at zero.  Calls whose GPU work overlaps (other
+ *   streams, or other threads without ordering) race on the array.
+ * Asynchronous on cuda_stream (NULL = legacy default stream).  Errors:
+ * SR_ERR_INVALID_ARG, SR_ERR_UNSUPPORTED (parameters or size), SR_ERR_CUDA. */
+sr_status sr_match_noalloc(const sr_params *params, double alpha0, double alpha1, double delta,
+                           const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
+                           float *d_disp, int16_t *d_wta_or_null, void *cuda_stream);
+
 /* 3-D reconstruction, Sec. II-D, for the left pixels of a full-disparity
  * map d_disp (W x H float, as written by sr_match).  d_xyz receives three
  * planes of W x H floats (X, then Y, then Z) in the camera frame of the

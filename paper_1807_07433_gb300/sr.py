@@ -25,7 +25,7 @@ SR_DEBUG_KEEP_AGG = 1
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
-           "sr_match_host", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
+           "sr_match_host", "sr_match_noalloc", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
            "sr_set_profiling", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
            "sr_status_str", "sr_last_error", "sr_version")
 
@@ -69,6 +69,8 @@ def load(path: str | None = None):
                 "sr_set_camera": (i, [vp, d, d, d, d]),
                 "sr_match": (i, [vp, vp, vp, i, vp, vp]),
                 "sr_match_host": (i, [vp, vp, vp, vp]),
+                "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
+                                         vp]),
                 "sr_reconstruct": (i, [vp, vp, vp]),
                 "sr_get_buffer": (i, [vp, i, vp, ctypes.POINTER(sz)]),
                 "sr_set_debug": (i, [vp, i]),
@@ -153,6 +155,17 @@ def sr_match(ctx, d_left, d_right, pitch_bytes: int, d_disp, d_wta_or_null=None)
 def sr_match_host(ctx, h_left, h_right, h_disp) -> None:
     _check(ctx, load().sr_match_host(ctx, _ptr(h_left), _ptr(h_right), _ptr(h_disp)),
            "sr_match_host")
+
+
+def sr_match_noalloc(params: sr_params, alpha0: float, alpha1: float, delta: float, d_left,
+                     d_right, pitch_bytes: int, d_disp, d_wta_or_null=None,
+                     cuda_stream=None) -> None:
+    """sr_match without a context and without any device allocation, for
+    callers that may not allocate (see include/sr.h for the size limit)."""
+    _check(None, load().sr_match_noalloc(ctypes.byref(params), alpha0, alpha1, delta,
+                                         _ptr(d_left), _ptr(d_right), int(pitch_bytes),
+                                         _ptr(d_disp), _ptr(d_wta_or_null),
+                                         _stream_handle(cuda_stream)), "sr_match_noalloc")
 
 
 def sr_reconstruct(ctx, d_disp, d_xyz) -> None:
