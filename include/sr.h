@@ -188,9 +188,21 @@ typedef enum {
 sr_status sr_get_buffer(sr_ctx *ctx, sr_buffer which, void *dst, size_t *bytes_inout);
 
 /* Debug flags (bit set).  SR_DEBUG_KEEP_AGG makes sr_match also store both
- * aggregated volumes (allocated on first use, 2*W*H*D floats). */
+ * aggregated volumes (allocated on first use, 2*W*H*D floats).
+ * SR_DEBUG_WITHHOLD_ROW is fault injection for the timeout path: the
+ * aggregation kernel withholds the copy of one cost row of every tile and
+ * shortens its bounded wait to ~1 ms, so the wait runs out, the results are
+ * garbage and the next synchronising call returns SR_ERR_TIMEOUT.  The GPU
+ * stays usable. */
 #define SR_DEBUG_KEEP_AGG 1
+#define SR_DEBUG_WITHHOLD_ROW 2
 sr_status sr_set_debug(sr_ctx *ctx, int flags);
+
+/* Wait for the context's queued work.  Device-side waits are bounded; when
+ * one ran out since the last check this returns SR_ERR_TIMEOUT (and clears
+ * the condition).  sr_match_host, sr_get_buffer and sr_stage_times check the
+ * same condition after they synchronise. */
+sr_status sr_synchronize(sr_ctx *ctx);
 
 /* Per-stage timing.  While enabled, sr_match records a CUDA event before
  * and after each stage on the context's stream.  sr_stage_times

@@ -8,24 +8,32 @@
 // Work decomposition (FP32 FMA-bound: 2*(2R+1)^2 flop per (u,v,d)):
 //   * a CTA owns a 32 x 4 pixel tile and ALL D disparities, so WTA and the
 //     parabola finish in the CTA and the aggregated volume never reaches HBM;
-//   * the weights of the tile's 128 pixels are computed once into shared
-//     memory (rows padded to a multiple of 4 for 128-bit loads);
-//   * the cost rows of the tile (+R halo columns) stream through a
-//     double-buffered shared-memory ring, one image row at a time, with
-//     asynchronous 16-byte copies (cp.async, zero-filled outside the image);
+//   * the tile's source rows (+R halo rows and columns) stream through a
+//     double-buffered shared-memory ring, one image row at a time: the cost
+//     row (one contiguous run of (32+2R)*D floats in the d-innermost volume)
+//     arrives by a single TMA bulk copy (cp.async.bulk) completing on an
+//     mbarrier per ring slot (columns outside the image are zeroed once);
+//     consumers wait with a bounded spin that records a timeout in an error
+//     word instead of hanging.  In the same step the CTA computes the weights
+//     that row needs -- tap row dy = y - v of each of the 4 output rows --
+//     into a second double-buffered ring laid out [row][dx][pixel], so one
+//     128-bit load gives one tap's weight for four adjacent pixels.  Each
+//     weight is computed exactly once, and shared memory stays ~36 KB per
+//     CTA, so four CTAs (16 warps) fit on an SM;
 //   * lane = pair of disparities (float2), D/2 lanes share one 8 x 4 pixel
 //     block, so the weights a lane needs are the same for all those lanes
 //     (shared-memory broadcast);
 //   * each thread accumulates 8 x 4 pixels x 2 disparities = 64 sums.  For
 //     every streamed source row it loads the (8+2R) cost pairs of the row
 //     into registers once and reuses each for up to (2R+1) pixels x up to
-//     4 output rows: ~10 FMAs per shared-memory cost load;
-//   * epilogue: the sums are transposed through shared memory so that each
-//     lane scans the D costs of one pixel: argmax (ties to the smallest d),
-//     then Eq. 12 on the neighbours of the winner.  The normalisation by
-//     sum_k w_k is a positive per-pixel scale, which changes neither the
-//     argmax nor the parabola vertex, so it is applied only when the
-//     aggregated volume is exported.
+//     4 output rows; taps are the outer loop and pixels the inner one, so
+//     each tap issues 16 independent FMAs (no dependent FMA chains);
+//   * epilogue: the sums are transposed through shared memory (over the
+//     rings) so that each lane scans the D costs of one pixel: argmax (ties
+//     to the smallest d), then Eq. 12 on the neighbours of the winner.  The
+//     normalisation by sum_k w_k is a positive per-pixel scale, which
+//     changes neither the argmax nor the parabola vertex, so it is applied
+//     only when the aggregated volume is exported.
 #pragma once
 #include "sr_internal.cuh"
 
@@ -39,70 +47,154 @@ struct AggCfg {
     static constexpr int G = 32 / SLOTS;           // pixel groups per warp
     static constexpr int NW = 4 / G;               // warps per CTA
     static constexpr int NT = 32 * NW;
+    static constexpr int MINB = 512 / NT;          // CTAs per SM to fit
     static constexpr int WS = 2 * R + 1;           // window side
-    static constexpr int WP = (WS + 3) / 4 * 4;    // padded weight row
-    static constexpr int PS = WS * WP;             // weight floats per pixel
     static constexpr int TXE = kAggTX + 2 * R;     // ring row width (pixels)
     static constexpr int TYE = kAggTY + 2 * R;     // source rows per tile
-    static constexpr int RING = TXE * D;           // floats per ring slot
-    static constexpr int WTS = kAggTY * (kAggTX * PS + 16);  // + bank skew
+    static constexpr int RING = TXE * D;           // floats per cost-ring slot
+    static constexpr int WRING = kAggTY * WS * kAggTX;  // floats per weight slot
+    static constexpr int RINGS = 2 * RING + 2 * WRING;
     static constexpr int EPI = kAggPix * (D + 1);  // epilogue transpose
-    static constexpr int UNION = WTS > EPI ? WTS : EPI;
+    static constexpr int UNION = RINGS > EPI ? RINGS : EPI;
     static constexpr int GUIDE = TYE * TXE;
     static constexpr size_t SMEM =
-        sizeof(float) * (2 * RING + UNION + ((GUIDE + 3) / 4 * 4) + kAggPix);
+        sizeof(float) * (UNION + ((GUIDE + 3) / 4 * 4) + kAggPix) + 2 * sizeof(unsigned long long);
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int n = valid ? 16 : 0;   // 0 source bytes => 16 zero bytes written
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
-
-// Weight offset (floats) of pixel (py, px) of the tile.  Block column
-// px/8 adds a 16-byte skew so that pixel groups of one warp that read the
-// weights of different blocks hit different shared-memory banks; each pixel
-// row gets 16 spare floats so that the skew never runs into the next row.
-__device__ __forceinline__ int wts_index(int py, int px, int PS) {
-    return py * (kAggTX * PS + 16) + px * PS + 4 * (px >> 3);
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// One-dimensional TMA copy global -> shared, completing on an mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Wait for the phase of the given parity; gives up after max_cycles SM clocks
+// (then records the timeout in *err and returns false).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          long long max_cycles, int *err) {
+    const unsigned a = smem_addr(bar);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > max_cycles) {
+            if (err) atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ float ex2_approx(float x) {   // 2^x, hardware approximation
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+    return y;
 }
 
 template <int R, int D, bool GU8>
-__global__ void __launch_bounds__(AggCfg<R, D>::NT)
+__global__ void __launch_bounds__(AggCfg<R, D>::NT, AggCfg<R, D>::MINB)
 k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
           const float *__restrict__ gf, int W, int H, float kd, float kr,
-          int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg) {
+          int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
+          int *__restrict__ err, long long wait_cycles, int withhold_last) {
     using C = AggCfg<R, D>;
     extern __shared__ __align__(16) float smem[];
-    float *ring = smem;                          // [2][TXE][D]
-    float *wts = ring + 2 * C::RING;             // [128][PS] (+skew); reused by epilogue
-    float *guide = wts + C::UNION;               // [TYE][TXE]
+    float *ring = smem;                          // [2][TXE][D] cost rows
+    float *wring = ring + 2 * C::RING;           // [2][4][WS][32] weights
+    float *guide = smem + C::UNION;              // [TYE][TXE]
     float *wsum = guide + (C::GUIDE + 3) / 4 * 4;  // [128]
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(wsum + kAggPix);  // [2]
 
     const int x0 = blockIdx.x * kAggTX, y0 = blockIdx.y * kAggTY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    auto load_row = [&](int j) {   // source row j of the tile -> ring slot j&1
+    // Columns of the tile's cost rows that lie inside the image; the rest of
+    // each ring slot is zeroed once (those neighbours have weight 0).
+    const int xs = max(x0 - R, 0), xe = min(x0 + kAggTX + R, W);
+    const unsigned row_bytes = (unsigned)((xe - xs) * D * sizeof(float));
+    // withhold_last (fault injection): no arrival and no copy for the last
+    // source row, whose wait then runs out; no later copy shares its slot,
+    // so nothing is in flight when the CTA exits.
+    auto issue_row = [&](int j) {   // thread 0: cost row of source row j -> slot j&1
         const int y = y0 - R + j;
-        if (y < 0 || y >= H) return;
-        float *dst = ring + (j & 1) * C::RING;
-        const float *src_row = vol + (size_t)y * W * D;
-        constexpr int CH = C::RING / 4;
-        for (int i = tid; i < CH; i += C::NT) {
-            const int c = (i * 4) / D;            // tile column of this chunk
-            const int x = x0 - R + c;
-            const bool ok = (x >= 0) && (x < W);
-            const int xc = clampi(x, 0, W - 1);
-            cp_async16(dst + i * 4, src_row + (size_t)xc * D + (i * 4) % D, ok);
+        unsigned long long *bar = bars + (j & 1);
+        if (withhold_last && j == C::TYE - 1) return;
+        if (y < 0 || y >= H) {
+            mbar_arrive(bar);   // no copy: complete the phase to keep the slot in step
+            return;
+        }
+        float *dst = ring + (j & 1) * C::RING + (xs - (x0 - R)) * D;
+        const float *src = vol + ((size_t)y * W + xs) * D;
+        mbar_arrive_expect_tx(bar, row_bytes);
+        tma_load_1d(dst, src, row_bytes, bar);
+    };
+
+    // Weights (Eqs. 9-10) that source row j contributes with: for output row
+    // py the tap row is dyi = j - py.  w = exp(-r^2/gd^2 - dg^2/gr^2)
+    // = exp2(-(r^2 kd + dg^2 kr)), zero for neighbours outside the image.
+    // Warp k computes rows py = k, k + NW, ...; lane = pixel column.
+    float wacc[4 / C::NW];
+#pragma unroll
+    for (int k = 0; k < 4 / C::NW; ++k) wacc[k] = 0.0f;
+    auto make_weights = [&](int j) {
+        float *wslot = wring + (j & 1) * C::WRING;
+#pragma unroll
+        for (int k = 0; k < 4 / C::NW; ++k) {
+            const int py = warp + k * C::NW;
+            const int dyi = j - py;
+            if (dyi < 0 || dyi >= C::WS) continue;
+            const int px = lane, u = x0 + px, v = y0 + py, y = v + dyi - R;
+            const bool rowok = (u < W) && (v < H) && (y >= 0) && (y < H);
+            const bool inner = rowok && (u - R >= 0) && (u + R < W);
+            const float gc = guide[(py + R) * C::TXE + px + R];
+            const float *grow = guide + (py + dyi) * C::TXE + px;
+            const float fy = (float)((dyi - R) * (dyi - R)) * kd;
+            float *wout = wslot + (py * C::WS) * kAggTX + px;
+            float s = 0.0f;
+#pragma unroll
+            for (int dxi = 0; dxi < C::WS; ++dxi) {
+                const float dg = grow[dxi] - gc;
+                float w = ex2_approx(-fmaf(dg * dg, kr, fmaf((float)((dxi - R) * (dxi - R)), kd, fy)));
+                if (!inner) {
+                    const int x = u + dxi - R;
+                    w = (rowok && x >= 0 && x < W) ? w : 0.0f;
+                }
+                wout[dxi * kAggTX] = w;
+                s += w;
+            }
+            wacc[k] += s;
         }
     };
 
-    // ---- prologue: guide tile, first cost row, weights ---------------------
+    // ---- prologue: barriers, guide tile, zeroed columns, first row ----------
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
     for (int i = tid; i < C::GUIDE; i += C::NT) {
         const int r = i / C::TXE, c = i % C::TXE;
         const int y = y0 - R + r, x = x0 - R + c;
@@ -111,37 +203,18 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
             g = GU8 ? (float)gl[(size_t)y * pitch + x] : gf[(size_t)y * W + x];
         guide[i] = g;
     }
-    load_row(0);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    __syncthreads();
-
-    for (int p = tid; p < kAggPix; p += C::NT) {
-        const int py = p / kAggTX, px = p % kAggTX;
-        const int u = x0 + px, v = y0 + py;
-        const bool pin = (u < W) && (v < H);
-        const float gc = guide[(py + R) * C::TXE + px + R];
-        float *wp = wts + wts_index(py, px, C::PS);
-        float s = 0.0f;
-        for (int dyi = 0; dyi < C::WS; ++dyi) {
-            const int y = v + dyi - R;
-            const bool yin = pin && (y >= 0) && (y < H);
-            const float *grow = guide + (py + dyi) * C::TXE + px;
-#pragma unroll
-            for (int dxi = 0; dxi < C::WP; ++dxi) {
-                float w = 0.0f;
-                const int x = u + dxi - R;
-                if (dxi < C::WS && yin && x >= 0 && x < W) {
-                    const float dg = grow[dxi] - gc;
-                    const float r2 = (float)((dxi - R) * (dxi - R) + (dyi - R) * (dyi - R));
-                    w = exp2f(-fmaf(r2, kd, dg * dg * kr));   // Eq. 9 x Eq. 10
-                }
-                wp[dyi * C::WP + dxi] = w;
-                s += w;
-            }
+    if (xs > x0 - R || xe < x0 + kAggTX + R) {
+        for (int i = tid; i < 2 * C::RING; i += C::NT) {
+            const int c = (i % C::RING) / D + x0 - R;
+            if (c < xs || c >= xe) ring[i] = 0.0f;
         }
-        wsum[p] = s > 0.0f ? s : 1.0f;
     }
-    cp_async_wait_all();
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        issue_row(0);
+    }
+    make_weights(0);
     __syncthreads();
 
     // ---- main loop: stream the tile's source rows --------------------------
@@ -157,11 +230,19 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
 
 #pragma unroll 1
     for (int j = 0; j < C::TYE; ++j) {
-        if (j + 1 < C::TYE) load_row(j + 1);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        if (j + 1 < C::TYE) {
+            if (tid == 0) {
+                // slot (j+1)&1 was last read before the barrier that ended step j-1
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                issue_row(j + 1);
+            }
+            make_weights(j + 1);
+        }
         const int y = y0 - R + j;
         if (y >= 0 && y < H) {
+            mbar_wait(bars + (j & 1), (unsigned)((j >> 1) & 1), wait_cycles, err);
             const float *rs = ring + (j & 1) * C::RING + bx * D + 2 * sl;
+            const float *ws = wring + (j & 1) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
 #pragma unroll
             for (int i = 0; i < kAggPX + 2 * R; ++i)
@@ -170,32 +251,31 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
             for (int py = 0; py < kAggTY; ++py) {
                 const int dyi = j - py;
                 if (dyi >= 0 && dyi < C::WS) {
-                    const float *wrow = wts + wts_index(py, bx, C::PS) + dyi * C::WP;
+                    const float *wb = ws + (py * C::WS) * kAggTX;
 #pragma unroll
-                    for (int px = 0; px < kAggPX; ++px) {
-                        float w[C::WP];
+                    for (int dx = 0; dx < C::WS; ++dx) {
+                        const float4 wa = *reinterpret_cast<const float4 *>(wb + dx * kAggTX);
+                        const float4 wc = *reinterpret_cast<const float4 *>(wb + dx * kAggTX + 4);
+                        const float w[kAggPX] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
 #pragma unroll
-                        for (int q = 0; q < C::WP; q += 4) {
-                            const float4 t = *reinterpret_cast<const float4 *>(wrow + px * C::PS + q);
-                            w[q] = t.x; w[q + 1] = t.y; w[q + 2] = t.z; w[q + 3] = t.w;
+                        for (int px = 0; px < kAggPX; ++px) {
+                            acc[py][px].x = fmaf(w[px], cst[px + dx].x, acc[py][px].x);
+                            acc[py][px].y = fmaf(w[px], cst[px + dx].y, acc[py][px].y);
                         }
-                        float2 a = acc[py][px];
-#pragma unroll
-                        for (int dx = 0; dx < C::WS; ++dx) {
-                            a.x = fmaf(w[dx], cst[px + dx].x, a.x);
-                            a.y = fmaf(w[dx], cst[px + dx].y, a.y);
-                        }
-                        acc[py][px] = a;
                     }
                 }
             }
         }
-        cp_async_wait_all();
         __syncthreads();
     }
 
-    // ---- epilogue: transpose, WTA, parabola ---------------------------------
-    float *E = wts + warp * (32 * C::G) * (D + 1);     // this warp's pixels x D
+    // ---- epilogue: transpose (over the rings), WTA, parabola ----------------
+#pragma unroll
+    for (int k = 0; k < 4 / C::NW; ++k) {
+        const float s = wacc[k];
+        wsum[(warp + k * C::NW) * kAggTX + lane] = s > 0.0f ? s : 1.0f;
+    }
+    float *E = smem + warp * (32 * C::G) * (D + 1);     // this warp's pixels x D
 #pragma unroll
     for (int py = 0; py < kAggTY; ++py)
 #pragma unroll
@@ -204,7 +284,7 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
             e[0] = acc[py][px].x;
             e[1] = acc[py][px].y;
         }
-    __syncwarp();
+    __syncthreads();
     for (int pw = lane; pw < 32 * C::G; pw += 32) {
         const int g = pw >> 5, py = (pw & 31) / kAggPX, px = pw % kAggPX;
         const int tpx = (warp * C::G + g) * kAggPX + px;
@@ -246,35 +326,29 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
 template <int R, int D>
 cudaError_t agg_launch_t(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
-                         cudaStream_t st) {
+                         const AggDebug &dbg, cudaStream_t st) {
     using C = AggCfg<R, D>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
-    if (gl) {
-        auto k = k_agg_wta<R, D, true>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        k<<<grid, C::NT, C::SMEM, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg);
-    } else {
-        auto k = k_agg_wta<R, D, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        k<<<grid, C::NT, C::SMEM, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg);
-    }
+    auto k = gl ? k_agg_wta<R, D, true> : k_agg_wta<R, D, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    k<<<grid, C::NT, C::SMEM, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
+                                    dbg.wait_cycles, dbg.withhold_last);
     return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t agg_launch_d(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub,
-                         float *agg, cudaStream_t st) {
+                         float *agg, const AggDebug &dbg, cudaStream_t st) {
     switch (agg_r) {
-        case 1: return agg_launch_t<1, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
-        case 2: return agg_launch_t<2, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
-        case 3: return agg_launch_t<3, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
-        case 4: return agg_launch_t<4, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
-        case 5: return agg_launch_t<5, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
-        case 6: return agg_launch_t<6, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
-        case 7: return agg_launch_t<7, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, st);
+        case 1: return agg_launch_t<1, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 2: return agg_launch_t<2, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 3: return agg_launch_t<3, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 4: return agg_launch_t<4, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 5: return agg_launch_t<5, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 6: return agg_launch_t<6, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 7: return agg_launch_t<7, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -2,7 +2,7 @@
 #include "k_agg.cuh"
 
 namespace sr {
-cudaError_t launch_agg_d64(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, cudaStream_t st) {
-    return agg_launch_d<64>(vol, gl, pitch, gf, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
+cudaError_t launch_agg_d64(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st) {
+    return agg_launch_d<64>(vol, gl, pitch, gf, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
 }
 }  // namespace sr

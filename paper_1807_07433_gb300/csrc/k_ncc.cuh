@@ -46,8 +46,11 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     constexpr int SW = kNccTX + 2 * RN + D - 1;  // sliding tile width
     constexpr int TH = kNccTY + 2 * RN;          // tile height
     constexpr int DC = D < 32 ? D : 32;          // disparity chunk held in registers
+    constexpr int XW = kNccTX + D - 1;           // sliding-block centres per tile row
     __shared__ float fix_s[TH][FW];
     __shared__ float sld_s[TH][SW];
+    __shared__ float smu_s[kNccTY][XW];          // sliding-block mean
+    __shared__ float sinv_s[kNccTY][XW];         // sliding-block 1/(n sigma)
 
     const int x0 = blockIdx.x * kNccTX, y0 = blockIdx.y * kNccTY;
     const int tid = threadIdx.x;
@@ -67,6 +70,20 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
         const float val = TARGET ? (float)left[(size_t)y * pitch + x] : rw[(size_t)y * W + x];
         sld_s[r][c] = val - kNccOffset;
     }
+    // Sliding-block statistics of the tile's rows.  In the extended stats rows
+    // (see launch_stats) the centres u-d (reference) and u+d (target) of the
+    // tile's pixels both occupy the index range [x0, x0 + 32 + D - 1).
+    {
+        const float *mu_s = TARGET ? mu_l : mu_r;
+        const float *inv_s = TARGET ? inv_l : inv_r;
+        for (int i = tid; i < kNccTY * XW; i += kNccThreads) {
+            const int r = i / XW, t = i % XW;
+            const int y = clampi(y0 + r, 0, H - 1);
+            const int xi = clampi(x0 + t, 0, WE - 1);
+            smu_s[r][t] = mu_s[(size_t)y * WE + xi];
+            sinv_s[r][t] = inv_s[(size_t)y * WE + xi];
+        }
+    }
     __syncthreads();
 
     const int tx = tid % kNccTX, ty = tid / kNccTX;
@@ -78,8 +95,9 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     const size_t rowo = (size_t)v * WE;
     const float *mu_f = TARGET ? mu_r + rowo + u + D - 1 : mu_l + rowo + u;
     const float *inv_fp = TARGET ? inv_r + rowo + u + D - 1 : inv_l + rowo + u;
-    const float *mu_s_row = TARGET ? mu_l + rowo + u : mu_r + rowo + u + D - 1;
-    const float *inv_s_row = TARGET ? inv_l + rowo + u : inv_r + rowo + u + D - 1;
+    // sliding centre of disparity d at smem index base + so, so = d or -d
+    const float *mu_s_row = &smu_s[ty][TARGET ? tx : tx + D - 1];
+    const float *inv_s_row = &sinv_s[ty][TARGET ? tx : tx + D - 1];
 
     // Centred fixed block and the sum of its (rounded) centred values.
     const float m = *mu_f;

@@ -17,11 +17,11 @@ cudaError_t launch_ncc_d32(bool, const uint8_t *, int, const float *, const floa
 cudaError_t launch_ncc_d64(bool, const uint8_t *, int, const float *, const float *, const float *,
                            const float *, const float *, int, int, int, float *, cudaStream_t);
 cudaError_t launch_agg_d16(const float *, const uint8_t *, int, const float *, int, int, int, float,
-                           float, int16_t *, float *, float *, cudaStream_t);
+                           float, int16_t *, float *, float *, const AggDebug &, cudaStream_t);
 cudaError_t launch_agg_d32(const float *, const uint8_t *, int, const float *, int, int, int, float,
-                           float, int16_t *, float *, float *, cudaStream_t);
+                           float, int16_t *, float *, float *, const AggDebug &, cudaStream_t);
 cudaError_t launch_agg_d64(const float *, const uint8_t *, int, const float *, int, int, int, float,
-                           float, int16_t *, float *, float *, cudaStream_t);
+                           float, int16_t *, float *, float *, const AggDebug &, cudaStream_t);
 
 bool ncc_supported(int D, int ncc_r) {
     return (D == 16 || D == 32 || D == 64) && ncc_r >= 1 && ncc_r <= 5;
@@ -44,13 +44,14 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
 
 cudaError_t launch_agg(const float *vol, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
-                       float gamma_r, int16_t *lbl, float *dsub, float *agg, cudaStream_t st) {
+                       float gamma_r, int16_t *lbl, float *dsub, float *agg,
+                       const AggDebug &dbg, cudaStream_t st) {
     const float log2e = 1.4426950408889634f;
     const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
     switch (D) {
-        case 16: return launch_agg_d16(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
-        case 32: return launch_agg_d32(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
-        case 64: return launch_agg_d64(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, st);
+        case 16: return launch_agg_d16(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
+        case 32: return launch_agg_d32(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
+        case 64: return launch_agg_d64(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -79,6 +80,7 @@ struct sr_ctx {
     uint8_t *stage_l = nullptr, *stage_r = nullptr;
     float *stage_disp = nullptr;
     int debug = 0;
+    int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
     bool matched = false, agg_valid = false;
     bool profiling = false, timed = false;
     cudaEvent_t ev[kStages + 1] = {};
@@ -106,7 +108,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(sr_ctx *c) {
     void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
                     c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
-                    c->stage_disp};
+                    c->stage_disp, c->d_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)
@@ -114,6 +116,27 @@ void free_all(sr_ctx *c) {
 }
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
+
+// After the stream is synchronised: report (and clear) a device-side timeout.
+sr_status take_device_error(sr_ctx *c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(err)");
+    if (h == 0) return SR_OK;
+    cudaMemset(c->d_err, 0, sizeof(int));
+    snprintf(c->err, sizeof(c->err), "a bounded device wait for a cost-row copy ran out");
+    return SR_ERR_TIMEOUT;
+}
+
+sr::AggDebug agg_debug(const sr_ctx *c) {
+    sr::AggDebug d;
+    d.err = c->d_err;
+    if (c->debug & SR_DEBUG_WITHHOLD_ROW) {
+        d.withhold_last = 1;
+        d.wait_cycles = 2000000;            // ~1 ms
+    }
+    return d;
+}
 
 }  // namespace
 
@@ -176,6 +199,8 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
     if (e == cudaSuccess) e = dalloc(&c->dsub, npx);
     if (e == cudaSuccess) e = dalloc(&c->lbl_l, npx);
     if (e == cudaSuccess) e = dalloc(&c->lbl_r, npx);
+    if (e == cudaSuccess) e = dalloc(&c->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     for (int i = 0; i <= kStages && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();   // clear a sticky allocation error
@@ -216,7 +241,7 @@ sr_status sr_set_camera(sr_ctx *c, double f_px, double baseline, double u0, doub
 }
 
 sr_status sr_set_debug(sr_ctx *c, int flags) {
-    if (!c || (flags & ~SR_DEBUG_KEEP_AGG)) return SR_ERR_INVALID_ARG;
+    if (!c || (flags & ~(SR_DEBUG_KEEP_AGG | SR_DEBUG_WITHHOLD_ROW))) return SR_ERR_INVALID_ARG;
     if ((flags & SR_DEBUG_KEEP_AGG) && !c->agg_l) {
         const size_t n = (size_t)c->p.width * c->p.height * c->p.max_disp;
         SR_TRY(c, dalloc(&c->agg_l, n), "cudaMalloc(agg_l)");
@@ -240,7 +265,13 @@ sr_status sr_stage_times(sr_ctx *c, float *ms, int n, int *count) {
     SR_TRY(c, cudaEventSynchronize(c->ev[kStages]), "cudaEventSynchronize");
     for (int i = 0; i < kStages && i < n; ++i)
         SR_TRY(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime");
-    return SR_OK;
+    return take_device_error(c);
+}
+
+sr_status sr_synchronize(sr_ctx *c) {
+    if (!c) return SR_ERR_INVALID_ARG;
+    SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+    return take_device_error(c);
 }
 
 sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
@@ -273,13 +304,14 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
                              c->inv_r, W, H, D, p.ncc_radius, c->vol_r, st),
            "ncc_tgt");
     SR_TRY(c, mark(), "cudaEventRecord");
+    const sr::AggDebug dbg = agg_debug(c);
     SR_TRY(c, sr::launch_agg(c->vol_l, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
                              p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
-                             st),
+                             dbg, st),
            "agg_ref");
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_agg(c->vol_r, nullptr, 0, c->rw, W, H, D, p.agg_radius, p.gamma_d,
-                             p.gamma_r, c->lbl_r, nullptr, keep ? c->agg_r : nullptr, st),
+                             p.gamma_r, c->lbl_r, nullptr, keep ? c->agg_r : nullptr, dbg, st),
            "agg_tgt");
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->alpha0, c->alpha1,
@@ -308,7 +340,7 @@ sr_status sr_match_host(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right
                               c->st),
            "D2H disp");
     SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
-    return SR_OK;
+    return take_device_error(c);
 }
 
 sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {
@@ -357,7 +389,7 @@ sr_status sr_get_buffer(sr_ctx *c, sr_buffer which, void *dst, size_t *bytes_ino
     SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
     SR_TRY(c, cudaMemcpy(dst, src, bytes, cudaMemcpyDefault), "cudaMemcpy");
     *bytes_inout = bytes;
-    return SR_OK;
+    return take_device_error(c);
 }
 
 }  // extern "C"

@@ -40,6 +40,16 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
                        const float *inv_r, int W, int H, int D, int ncc_r, float *vol,
                        cudaStream_t st);
 
+// Bounded-wait settings of the aggregation kernel.  err (nullable) receives 1
+// when a wait for a cost-row copy runs out after wait_cycles SM clocks;
+// withhold_last = 1 withholds the copy of the last source row of every tile
+// (a test of the timeout path), 0 in normal use.
+struct AggDebug {
+    int *err = nullptr;
+    long long wait_cycles = 2000000000LL;   // ~1 s at 2 GHz
+    int withhold_last = 0;
+};
+
 // Eqs. 8-10 bilateral aggregation fused with WTA (Sec. II-B-3) and, for the
 // reference view, the Eq. 12 parabola.  Guide: the left image (uint8, when
 // guide_u8 != nullptr) or the warped target (float).  Writes lbl [H][W]
@@ -47,7 +57,8 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
 // aggregated volume agg [H][W][D] (nullable).
 cudaError_t launch_agg(const float *vol, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
-                       float gamma_r, int16_t *lbl, float *dsub, float *agg, cudaStream_t st);
+                       float gamma_r, int16_t *lbl, float *dsub, float *agg,
+                       const AggDebug &dbg, cudaStream_t st);
 
 // Eq. 11 check with tolerance, then Sec. II-C post-processing.
 cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,

@@ -102,6 +102,7 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     int16_t *lbl_r = reinterpret_cast<int16_t *>(take(b_lbl));
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    const sr::AggDebug dbg;   // default bounded waits; no error word to report through
     const int Wi = p.width, Hi = p.height, Di = p.max_disp;
     if (sr::launch_warp(d_right, pitch_bytes, Wi, Hi, alpha0, alpha1, delta, rw, st) != cudaSuccess ||
         sr::launch_stats(d_left, pitch_bytes, rw, Wi, Hi, Di, p.ncc_radius, mu_l, inv_l, mu_r,
@@ -111,9 +112,9 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
         sr::launch_ncc(true, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
                        p.ncc_radius, vol_r, st) != cudaSuccess ||
         sr::launch_agg(vol_l, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius, p.gamma_d,
-                       p.gamma_r, lbl_l, dsub, nullptr, st) != cudaSuccess ||
+                       p.gamma_r, lbl_l, dsub, nullptr, dbg, st) != cudaSuccess ||
         sr::launch_agg(vol_r, nullptr, 0, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d, p.gamma_r,
-                       lbl_r, nullptr, nullptr, st) != cudaSuccess ||
+                       lbl_r, nullptr, nullptr, dbg, st) != cudaSuccess ||
         sr::launch_lrc_post(lbl_l, lbl_r, dsub, Wi, Hi, alpha0, alpha1, delta, p.lr_thresh,
                             d_disp, d_wta_or_null, st) != cudaSuccess)
         return SR_ERR_CUDA;

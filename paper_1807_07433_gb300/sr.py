@@ -22,11 +22,12 @@ SR_VOL_F32, SR_VOL_F16, SR_VOL_BF16 = range(3)
 (SR_BUF_WARPED, SR_BUF_MU_L, SR_BUF_INV_L, SR_BUF_MU_R, SR_BUF_INV_R, SR_BUF_COST_L,
  SR_BUF_COST_R, SR_BUF_AGG_L, SR_BUF_AGG_R, SR_BUF_WTA_L, SR_BUF_WTA_R, SR_BUF_DSUB) = range(12)
 SR_DEBUG_KEEP_AGG = 1
+SR_DEBUG_WITHHOLD_ROW = 2
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
            "sr_match_host", "sr_match_noalloc", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
-           "sr_set_profiling", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
+           "sr_set_profiling", "sr_synchronize", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
            "sr_status_str", "sr_last_error", "sr_version")
 
 
@@ -75,6 +76,7 @@ def load(path: str | None = None):
                 "sr_get_buffer": (i, [vp, i, vp, ctypes.POINTER(sz)]),
                 "sr_set_debug": (i, [vp, i]),
                 "sr_set_profiling": (i, [vp, i]),
+                "sr_synchronize": (i, [vp]),
                 "sr_stage_times": (i, [vp, ctypes.POINTER(f), i, ctypes.POINTER(i)]),
                 "sr_stage_names": (ctypes.c_char_p, []),
                 "sr_kernels_per_match": (i, [vp]),
@@ -185,6 +187,10 @@ def sr_set_debug(ctx, flags: int) -> None:
 
 def sr_set_profiling(ctx, enable: bool) -> None:
     _check(ctx, load().sr_set_profiling(ctx, int(bool(enable))), "sr_set_profiling")
+
+
+def sr_synchronize(ctx) -> None:
+    _check(ctx, load().sr_synchronize(ctx), "sr_synchronize")
 
 
 def sr_stage_times(ctx) -> dict:

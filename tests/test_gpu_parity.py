@@ -216,3 +216,30 @@ def test_error_paths_on_device():
         torch.cuda.synchronize()
         assert int(m.buffer(sr.SR_BUF_WTA_L).max()) == 0
         assert np.all(m.buffer(sr.SR_BUF_COST_L) == 0.0)
+
+
+def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
+    """Failure detection without a GPU fault: the aggregation kernel is told to
+    withhold one cost-row copy, its bounded wait runs out, the host gets
+    SR_ERR_TIMEOUT, and the same context then matches correctly again."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    w = CASES[0]
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    good = run_gpu(w, left, right)
+    dl, dr = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        sr.sr_set_debug(m.ctx, sr.SR_DEBUG_WITHHOLD_ROW)
+        m.match(dl, dr)
+        with pytest.raises(sr.SrError) as e:
+            sr.sr_synchronize(m.ctx)
+        assert e.value.status == sr.SR_ERR_TIMEOUT
+        sr.sr_synchronize(m.ctx)          # the condition was cleared
+        sr.sr_set_debug(m.ctx, 0)
+        wta = torch.empty((H, W), dtype=torch.int16, device="cuda")
+        m.match(dl, dr, wta=wta)
+        sr.sr_synchronize(m.ctx)
+        np.testing.assert_array_equal(wta.cpu().numpy(), good["wta"])
