@@ -54,7 +54,9 @@ typedef enum {
     SR_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
 } sr_status;
 
-/* Storage type of the staged cost volumes.  All arithmetic is FP32. */
+/* Storage type of the staged cost volumes.  All arithmetic is FP32: NCC
+ * costs are computed in FP32 and rounded to nearest when stored; the
+ * aggregation widens them back to FP32 and accumulates in FP32. */
 typedef enum { SR_VOL_F32 = 0, SR_VOL_F16 = 1, SR_VOL_BF16 = 2 } sr_vol_dtype;
 
 /* Method parameters, fixed for the lifetime of a context.
@@ -85,7 +87,8 @@ typedef struct sr_ctx sr_ctx;   /* opaque; owns only its device scratch */
 /* Create a context on the current device.  cuda_stream is the cudaStream_t
  * all work is queued on (NULL = legacy default stream).  Allocates the
  * context's scratch: warped image, block statistics, the two cost volumes
- * and the per-pixel maps (about W*H*(2*D*4 + 40) bytes for FP32 volumes).
+ * and the per-pixel maps (about W*H*(2*D*e + 40) bytes, e = 4 bytes per
+ * stored cost for SR_VOL_F32 and 2 for SR_VOL_F16 / SR_VOL_BF16).
  * Errors: SR_ERR_INVALID_ARG (null out, non-positive sizes or constants),
  * SR_ERR_UNSUPPORTED (D, radii outside the supported set), SR_ERR_OOM,
  * SR_ERR_CUDA.  On error *out is set to NULL. */
@@ -136,10 +139,11 @@ sr_status sr_match_host(sr_ctx *ctx, const uint8_t *h_left, const uint8_t *h_rig
  * the process exits.  Inputs, outputs and parameters have the meaning they
  * have for sr_create + sr_set_plane + sr_match; d_disp receives the same
  * values sr_match writes.
- *   Size limit: with A(b) = b rounded up to a multiple of 256,
- *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + 2*A(4*W*H*D) + 2*A(2*W*H) <= 32 MiB
- *   (e.g. 480x360 at D = 16, 320x180 at D = 64); larger frames are rejected
- *   with SR_ERR_UNSUPPORTED before any GPU work.
+ *   Size limit: with A(b) = b rounded up to a multiple of 256 and e the
+ *   bytes of one stored cost (4 for SR_VOL_F32, 2 for SR_VOL_F16/BF16),
+ *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + 2*A(e*W*H*D) + 2*A(2*W*H) <= 32 MiB
+ *   (e.g. 480x360 at D = 16, 320x180 at D = 64 with FP32 volumes); larger
+ *   frames are rejected with SR_ERR_UNSUPPORTED before any GPU work.
  *   The first call on a device looks up the array's device address with
  *   cudaGetSymbolAddress (with that device current); make that first call
  *   before any stream capture.

@@ -41,7 +41,7 @@ namespace sr {
 
 constexpr int kAggTX = 32, kAggTY = 4, kAggPX = 8, kAggPix = kAggTX * kAggTY;
 
-template <int R, int D>
+template <int R, int D, typename VT>
 struct AggCfg {
     static constexpr int SLOTS = D / 2;            // lanes per pixel group
     static constexpr int G = 32 / SLOTS;           // pixel groups per warp
@@ -51,14 +51,17 @@ struct AggCfg {
     static constexpr int WS = 2 * R + 1;           // window side
     static constexpr int TXE = kAggTX + 2 * R;     // ring row width (pixels)
     static constexpr int TYE = kAggTY + 2 * R;     // source rows per tile
-    static constexpr int RING = TXE * D;           // floats per cost-ring slot
+    static constexpr int RING = TXE * D;           // elements per cost-ring slot
     static constexpr int WRING = kAggTY * WS * kAggTX;  // floats per weight slot
-    static constexpr int RINGS = 2 * RING + 2 * WRING;
-    static constexpr int EPI = kAggPix * (D + 1);  // epilogue transpose
-    static constexpr int UNION = RINGS > EPI ? RINGS : EPI;
+    // shared memory, in bytes: [cost ring | weight ring] (reused by the
+    // epilogue transpose), guide tile, weight sums, two mbarriers
+    static constexpr size_t RINGB = 2 * (size_t)RING * sizeof(VT);
+    static constexpr size_t RINGSB = RINGB + 2 * (size_t)WRING * sizeof(float);
+    static constexpr size_t EPIB = (size_t)kAggPix * (D + 1) * sizeof(float);
+    static constexpr size_t UNIONB = ((RINGSB > EPIB ? RINGSB : EPIB) + 15) / 16 * 16;
     static constexpr int GUIDE = TYE * TXE;
-    static constexpr size_t SMEM =
-        sizeof(float) * (UNION + ((GUIDE + 3) / 4 * 4) + kAggPix) + 2 * sizeof(unsigned long long);
+    static constexpr size_t SMEM = UNIONB + sizeof(float) * ((GUIDE + 3) / 4 * 4 + kAggPix) +
+                                   2 * sizeof(unsigned long long);
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
 };
 
@@ -114,17 +117,18 @@ __device__ __forceinline__ float ex2_approx(float x) {   // 2^x, hardware approx
     return y;
 }
 
-template <int R, int D, bool GU8>
-__global__ void __launch_bounds__(AggCfg<R, D>::NT, AggCfg<R, D>::MINB)
-k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
+template <int R, int D, bool GU8, typename VT>
+__global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
+k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
           const float *__restrict__ gf, int W, int H, float kd, float kr,
           int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
           int *__restrict__ err, long long wait_cycles, int withhold_last) {
-    using C = AggCfg<R, D>;
-    extern __shared__ __align__(16) float smem[];
-    float *ring = smem;                          // [2][TXE][D] cost rows
-    float *wring = ring + 2 * C::RING;           // [2][4][WS][32] weights
-    float *guide = smem + C::UNION;              // [TYE][TXE]
+    using C = AggCfg<R, D, VT>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *smem = reinterpret_cast<float *>(smem_raw);            // epilogue view
+    VT *ring = reinterpret_cast<VT *>(smem_raw);                  // [2][TXE][D] cost rows
+    float *wring = reinterpret_cast<float *>(smem_raw + C::RINGB);  // [2][4][WS][32] weights
+    float *guide = reinterpret_cast<float *>(smem_raw + C::UNIONB);  // [TYE][TXE]
     float *wsum = guide + (C::GUIDE + 3) / 4 * 4;  // [128]
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(wsum + kAggPix);  // [2]
 
@@ -134,7 +138,7 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
     // Columns of the tile's cost rows that lie inside the image; the rest of
     // each ring slot is zeroed once (those neighbours have weight 0).
     const int xs = max(x0 - R, 0), xe = min(x0 + kAggTX + R, W);
-    const unsigned row_bytes = (unsigned)((xe - xs) * D * sizeof(float));
+    const unsigned row_bytes = (unsigned)((xe - xs) * D * sizeof(VT));
     // withhold_last (fault injection): no arrival and no copy for the last
     // source row, whose wait then runs out; no later copy shares its slot,
     // so nothing is in flight when the CTA exits.
@@ -146,8 +150,8 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
             mbar_arrive(bar);   // no copy: complete the phase to keep the slot in step
             return;
         }
-        float *dst = ring + (j & 1) * C::RING + (xs - (x0 - R)) * D;
-        const float *src = vol + ((size_t)y * W + xs) * D;
+        VT *dst = ring + (j & 1) * C::RING + (xs - (x0 - R)) * D;
+        const VT *src = vol + ((size_t)y * W + xs) * D;
         mbar_arrive_expect_tx(bar, row_bytes);
         tma_load_1d(dst, src, row_bytes, bar);
     };
@@ -206,7 +210,7 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
     if (xs > x0 - R || xe < x0 + kAggTX + R) {
         for (int i = tid; i < 2 * C::RING; i += C::NT) {
             const int c = (i % C::RING) / D + x0 - R;
-            if (c < xs || c >= xe) ring[i] = 0.0f;
+            if (c < xs || c >= xe) ring[i] = VT(0.0f);
         }
     }
     __syncthreads();
@@ -241,12 +245,12 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
         const int y = y0 - R + j;
         if (y >= 0 && y < H) {
             mbar_wait(bars + (j & 1), (unsigned)((j >> 1) & 1), wait_cycles, err);
-            const float *rs = ring + (j & 1) * C::RING + bx * D + 2 * sl;
+            const VT *rs = ring + (j & 1) * C::RING + bx * D + 2 * sl;
             const float *ws = wring + (j & 1) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
 #pragma unroll
             for (int i = 0; i < kAggPX + 2 * R; ++i)
-                cst[i] = *reinterpret_cast<const float2 *>(rs + i * D);
+                cst[i] = load_pair(rs + i * D);
 #pragma unroll
             for (int py = 0; py < kAggTY; ++py) {
                 const int dyi = j - py;
@@ -323,13 +327,13 @@ k_agg_wta(const float *__restrict__ vol, const uint8_t *__restrict__ gl, int pit
     }
 }
 
-template <int R, int D>
-cudaError_t agg_launch_t(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W,
+template <int R, int D, typename VT>
+cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
                          const AggDebug &dbg, cudaStream_t st) {
-    using C = AggCfg<R, D>;
+    using C = AggCfg<R, D, VT>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
-    auto k = gl ? k_agg_wta<R, D, true> : k_agg_wta<R, D, false>;
+    auto k = gl ? k_agg_wta<R, D, true, VT> : k_agg_wta<R, D, false, VT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
@@ -337,18 +341,18 @@ cudaError_t agg_launch_t(const float *vol, const uint8_t *gl, int pitch, const f
     return cudaGetLastError();
 }
 
-template <int D>
-cudaError_t agg_launch_d(const float *vol, const uint8_t *gl, int pitch, const float *gf, int W,
+template <int D, typename VT>
+cudaError_t agg_launch_d(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub,
                          float *agg, const AggDebug &dbg, cudaStream_t st) {
     switch (agg_r) {
-        case 1: return agg_launch_t<1, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 2: return agg_launch_t<2, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 3: return agg_launch_t<3, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 4: return agg_launch_t<4, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 5: return agg_launch_t<5, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 6: return agg_launch_t<6, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 7: return agg_launch_t<7, D>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 1: return agg_launch_t<1, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 2: return agg_launch_t<2, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 3: return agg_launch_t<3, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 4: return agg_launch_t<4, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 5: return agg_launch_t<5, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 6: return agg_launch_t<6, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
+        case 7: return agg_launch_t<7, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
         default: return cudaErrorInvalidValue;
     }
 }

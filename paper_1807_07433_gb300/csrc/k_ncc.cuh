@@ -35,12 +35,12 @@ namespace sr {
 
 constexpr int kNccTX = 32, kNccTY = 4, kNccThreads = kNccTX * kNccTY;
 
-template <int RN, int D, bool TARGET>
+template <int RN, int D, bool TARGET, typename VT>
 __global__ void __launch_bounds__(kNccThreads)
 k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
       const float *__restrict__ mu_l, const float *__restrict__ inv_l,
       const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
-      float *__restrict__ vol) {
+      VT *__restrict__ vol) {
     constexpr int B = 2 * RN + 1;
     constexpr int FW = kNccTX + 2 * RN;          // fixed tile width
     constexpr int SW = kNccTX + 2 * RN + D - 1;  // sliding tile width
@@ -114,7 +114,7 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     // n/(n sigma_f) of the fixed block (Eq. 3 divides n*cov by n*sigma_f*sigma_s).
     constexpr float n = (float)(B * B);
     const float inv_f = n * *inv_fp;
-    float *out = vol + ((size_t)v * W + u) * D;
+    VT *out = vol + ((size_t)v * W + u) * D;
 
 #pragma unroll 1
     for (int d0 = 0; d0 < D; d0 += DC) {
@@ -151,35 +151,33 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
             cst[i] = num * inv_f * inv_s_row[so];
         }
 #pragma unroll
-        for (int i = 0; i < DC; i += 4)
-            *reinterpret_cast<float4 *>(out + d0 + i) =
-                make_float4(cst[i], cst[i + 1], cst[i + 2], cst[i + 3]);
+        for (int i = 0; i < DC; i += 8) store8(out + d0 + i, cst + i);
     }
 }
 
-template <int RN, int D>
+template <int RN, int D, typename VT>
 cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
-                         const float *inv_r, int W, int H, float *vol, cudaStream_t st) {
+                         const float *inv_r, int W, int H, VT *vol, cudaStream_t st) {
     const dim3 grid((W + kNccTX - 1) / kNccTX, (H + kNccTY - 1) / kNccTY);
     if (target)
-        k_ncc<RN, D, true><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
+        k_ncc<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
     else
-        k_ncc<RN, D, false><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
+        k_ncc<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
     return cudaGetLastError();
 }
 
-template <int D>
+template <int D, typename VT>
 cudaError_t ncc_launch_d(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
-                         const float *inv_r, int W, int H, int ncc_r, float *vol,
+                         const float *inv_r, int W, int H, int ncc_r, VT *vol,
                          cudaStream_t st) {
     switch (ncc_r) {
-        case 1: return ncc_launch_t<1, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 2: return ncc_launch_t<2, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 3: return ncc_launch_t<3, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 4: return ncc_launch_t<4, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 5: return ncc_launch_t<5, D>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 1: return ncc_launch_t<1, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 2: return ncc_launch_t<2, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 3: return ncc_launch_t<3, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 4: return ncc_launch_t<4, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
+        case 5: return ncc_launch_t<5, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -2,6 +2,7 @@
 // ownership, stage sequencing on the caller's stream, timing and errors.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -10,18 +11,24 @@
 #include "sr_internal.cuh"
 
 namespace sr {
-cudaError_t launch_ncc_d16(bool, const uint8_t *, int, const float *, const float *, const float *,
-                           const float *, const float *, int, int, int, float *, cudaStream_t);
-cudaError_t launch_ncc_d32(bool, const uint8_t *, int, const float *, const float *, const float *,
-                           const float *, const float *, int, int, int, float *, cudaStream_t);
-cudaError_t launch_ncc_d64(bool, const uint8_t *, int, const float *, const float *, const float *,
-                           const float *, const float *, int, int, int, float *, cudaStream_t);
-cudaError_t launch_agg_d16(const float *, const uint8_t *, int, const float *, int, int, int, float,
-                           float, int16_t *, float *, float *, const AggDebug &, cudaStream_t);
-cudaError_t launch_agg_d32(const float *, const uint8_t *, int, const float *, int, int, int, float,
-                           float, int16_t *, float *, float *, const AggDebug &, cudaStream_t);
-cudaError_t launch_agg_d64(const float *, const uint8_t *, int, const float *, int, int, int, float,
-                           float, int16_t *, float *, float *, const AggDebug &, cudaStream_t);
+cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d16_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d16_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d32_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d64_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
 
 bool ncc_supported(int D, int ncc_r) {
     return (D == 16 || D == 32 || D == 64) && ncc_r >= 1 && ncc_r <= 5;
@@ -30,28 +37,36 @@ bool agg_supported(int D, int agg_r) {
     return (D == 16 || D == 32 || D == 64) && agg_r >= 1 && agg_r <= 7;
 }
 
+#define SR_VT_DISPATCH(FN, D, vt, ...)                              \
+    switch (vt) {                                                   \
+        case kVolF32: return FN##_d##D##_f32(__VA_ARGS__);          \
+        case kVolF16: return FN##_d##D##_f16(__VA_ARGS__);          \
+        case kVolBF16: return FN##_d##D##_bf16(__VA_ARGS__);        \
+        default: return cudaErrorInvalidValue;                      \
+    }
+
 cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
                        const float *mu_l, const float *inv_l, const float *mu_r,
-                       const float *inv_r, int W, int H, int D, int ncc_r, float *vol,
+                       const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
                        cudaStream_t st) {
     switch (D) {
-        case 16: return launch_ncc_d16(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st);
-        case 32: return launch_ncc_d32(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st);
-        case 64: return launch_ncc_d64(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st);
+        case 16: SR_VT_DISPATCH(launch_ncc, 16, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st)
+        case 32: SR_VT_DISPATCH(launch_ncc, 32, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st)
+        case 64: SR_VT_DISPATCH(launch_ncc, 64, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st)
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_agg(const float *vol, const uint8_t *guide_u8, int pitch,
+cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
                        const AggDebug &dbg, cudaStream_t st) {
     const float log2e = 1.4426950408889634f;
     const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
     switch (D) {
-        case 16: return launch_agg_d16(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
-        case 32: return launch_agg_d32(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
-        case 64: return launch_agg_d64(vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st);
+        case 16: SR_VT_DISPATCH(launch_agg, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st)
+        case 32: SR_VT_DISPATCH(launch_agg, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st)
+        case 64: SR_VT_DISPATCH(launch_agg, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st)
         default: return cudaErrorInvalidValue;
     }
 }
@@ -74,7 +89,8 @@ struct sr_ctx {
     bool camera = false;
     // scratch (owned)
     float *rw = nullptr, *mu_l = nullptr, *inv_l = nullptr, *mu_r = nullptr, *inv_r = nullptr;
-    float *vol_l = nullptr, *vol_r = nullptr, *dsub = nullptr;
+    void *vol_l = nullptr, *vol_r = nullptr;   // cost volumes, element type p.vol_dtype
+    float *dsub = nullptr;
     int16_t *lbl_l = nullptr, *lbl_r = nullptr;
     float *agg_l = nullptr, *agg_r = nullptr;
     uint8_t *stage_l = nullptr, *stage_r = nullptr;
@@ -116,6 +132,23 @@ void free_all(sr_ctx *c) {
 }
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
+
+// IEEE 754 binary16 bit pattern -> float (sign, 5-bit exponent, 10-bit fraction).
+float half_bits_to_float(uint16_t h) {
+    const int s = h >> 15, e = (h >> 10) & 0x1f, m = h & 0x3ff;
+    float v;
+    if (e == 0) v = ldexpf((float)m, -24);                      // subnormal: m * 2^-24
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexpf((float)(m | 0x400), e - 25);                // (1024 + m) * 2^(e-25)
+    return s ? -v : v;
+}
+// bfloat16 is the upper half of a binary32 pattern.
+float bf16_bits_to_float(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float v;
+    memcpy(&v, &u, sizeof(v));
+    return v;
+}
 
 // After the stream is synchronised: report (and clear) a device-side timeout.
 sr_status take_device_error(sr_ctx *c) {
@@ -177,8 +210,7 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
         return SR_ERR_INVALID_ARG;
     if (p.vol_dtype != SR_VOL_F32 && p.vol_dtype != SR_VOL_F16 && p.vol_dtype != SR_VOL_BF16)
         return SR_ERR_INVALID_ARG;
-    if (!sr::ncc_supported(p.max_disp, p.ncc_radius) || !sr::agg_supported(p.max_disp, p.agg_radius) ||
-        p.vol_dtype != SR_VOL_F32)
+    if (!sr::ncc_supported(p.max_disp, p.ncc_radius) || !sr::agg_supported(p.max_disp, p.agg_radius))
         return SR_ERR_UNSUPPORTED;
 
     sr_ctx *c = new (std::nothrow) sr_ctx();
@@ -194,8 +226,9 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
     if (e == cudaSuccess) e = dalloc(&c->mu_r, H * WE);
     if (e == cudaSuccess) e = dalloc(&c->inv_l, H * WE);
     if (e == cudaSuccess) e = dalloc(&c->inv_r, H * WE);
-    if (e == cudaSuccess) e = dalloc(&c->vol_l, npx * D);
-    if (e == cudaSuccess) e = dalloc(&c->vol_r, npx * D);
+    const size_t vbytes = npx * D * sr::vol_elem_bytes(p.vol_dtype);
+    if (e == cudaSuccess) e = cudaMalloc(&c->vol_l, vbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->vol_r, vbytes);
     if (e == cudaSuccess) e = dalloc(&c->dsub, npx);
     if (e == cudaSuccess) e = dalloc(&c->lbl_l, npx);
     if (e == cudaSuccess) e = dalloc(&c->lbl_r, npx);
@@ -297,20 +330,20 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
            "stats");
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, st),
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st),
            "ncc_ref");
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_ncc(true, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, st),
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, p.vol_dtype, st),
            "ncc_tgt");
     SR_TRY(c, mark(), "cudaEventRecord");
     const sr::AggDebug dbg = agg_debug(c);
-    SR_TRY(c, sr::launch_agg(c->vol_l, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
+    SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
                              p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
                              dbg, st),
            "agg_ref");
     SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_agg(c->vol_r, nullptr, 0, c->rw, W, H, D, p.agg_radius, p.gamma_d,
+    SR_TRY(c, sr::launch_agg(c->vol_r, p.vol_dtype, nullptr, 0, c->rw, W, H, D, p.agg_radius, p.gamma_d,
                              p.gamma_r, c->lbl_r, nullptr, keep ? c->agg_r : nullptr, dbg, st),
            "agg_tgt");
     SR_TRY(c, mark(), "cudaEventRecord");
@@ -375,8 +408,33 @@ sr_status sr_get_buffer(sr_ctx *c, sr_buffer which, void *dst, size_t *bytes_ino
             *bytes_inout = npx * 4;
             return SR_OK;
         }
-        case SR_BUF_COST_L: src = c->vol_l; bytes = npx * D * 4; break;
-        case SR_BUF_COST_R: src = c->vol_r; bytes = npx * D * 4; break;
+        case SR_BUF_COST_L: case SR_BUF_COST_R: {
+            const size_t n = npx * D;
+            if (*bytes_inout < n * 4) { *bytes_inout = n * 4; return SR_ERR_INVALID_ARG; }
+            if (!c->matched) return SR_ERR_STATE;
+            const void *v = which == SR_BUF_COST_L ? c->vol_l : c->vol_r;
+            SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+            if (c->p.vol_dtype == SR_VOL_F32) {
+                SR_TRY(c, cudaMemcpy(dst, v, n * 4, cudaMemcpyDefault), "cudaMemcpy");
+            } else {
+                // widen the 16-bit volume to float on the host
+                uint16_t *raw = (uint16_t *)malloc(n * 2);
+                float *wide = (float *)malloc(n * 4);
+                if (!raw || !wide) { free(raw); free(wide); return SR_ERR_OOM; }
+                cudaError_t e = cudaMemcpy(raw, v, n * 2, cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess) {
+                    for (size_t i = 0; i < n; ++i)
+                        wide[i] = c->p.vol_dtype == SR_VOL_F16 ? half_bits_to_float(raw[i])
+                                                               : bf16_bits_to_float(raw[i]);
+                    e = cudaMemcpy(dst, wide, n * 4, cudaMemcpyDefault);
+                }
+                free(raw);
+                free(wide);
+                if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(volume)");
+            }
+            *bytes_inout = n * 4;
+            return take_device_error(c);
+        }
         case SR_BUF_AGG_L: src = c->agg_valid ? c->agg_l : nullptr; bytes = npx * D * 4; break;
         case SR_BUF_AGG_R: src = c->agg_valid ? c->agg_r : nullptr; bytes = npx * D * 4; break;
         case SR_BUF_WTA_L: src = c->lbl_l; bytes = npx * 2; break;

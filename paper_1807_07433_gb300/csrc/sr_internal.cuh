@@ -1,6 +1,8 @@
 // sr_internal.cuh -- launchers shared by the kernel translation units and the
 // C ABI layer (sr_api.cu).  Not installed; the public interface is sr.h.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,6 +15,37 @@ constexpr float kNccOffset = 128.0f;
 
 // Variance below which a block counts as flat (NCC = 0).
 constexpr float kFlatVar = 1e-6f;
+
+// Storage type of the cost volumes (values of sr_vol_dtype).
+enum VolType { kVolF32 = 0, kVolF16 = 1, kVolBF16 = 2 };
+inline size_t vol_elem_bytes(int vt) { return vt == kVolF32 ? 4 : 2; }
+
+// Loads of two adjacent stored costs, widened to FP32, and stores of eight.
+__device__ __forceinline__ float2 load_pair(const float *p) {
+    return *reinterpret_cast<const float2 *>(p);
+}
+__device__ __forceinline__ float2 load_pair(const __half *p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+__device__ __forceinline__ float2 load_pair(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+__device__ __forceinline__ void store8(float *p, const float *v) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void store8(__half *p, const float *v) {
+    __half2 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(h);
+}
+__device__ __forceinline__ void store8(__nv_bfloat16 *p, const float *v) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(h);
+}
 
 // Supported compile-time parameter sets.
 bool ncc_supported(int D, int ncc_r);
@@ -32,12 +65,13 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
                          int ncc_r, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
                          cudaStream_t st);
 
-// Eq. 3 cost volume [H][W][D] (float).  target = false: reference volume
+// Eq. 3 cost volume [H][W][D], stored as vt (VolType; FP32 arithmetic,
+// rounded to nearest on store).  target = false: reference volume
 // c(u,v,d) = NCC(left block u, warped-target block u-d); target = true:
 // target volume c(u,v,d) = NCC(left block u+d, warped-target block u).
 cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
                        const float *mu_l, const float *inv_l, const float *mu_r,
-                       const float *inv_r, int W, int H, int D, int ncc_r, float *vol,
+                       const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
                        cudaStream_t st);
 
 // Bounded-wait settings of the aggregation kernel.  err (nullable) receives 1
@@ -55,7 +89,7 @@ struct AggDebug {
 // guide_u8 != nullptr) or the warped target (float).  Writes lbl [H][W]
 // int16, dsub [H][W] float (nullable) and, for inspection, the normalised
 // aggregated volume agg [H][W][D] (nullable).
-cudaError_t launch_agg(const float *vol, const uint8_t *guide_u8, int pitch,
+cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
                        const AggDebug &dbg, cudaStream_t st);

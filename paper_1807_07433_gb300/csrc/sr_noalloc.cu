@@ -74,14 +74,15 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
         pitch_bytes < p.width || !isfinite(alpha0) || !isfinite(alpha1) || !isfinite(delta))
         return SR_ERR_INVALID_ARG;
     if (!sr::ncc_supported(p.max_disp, p.ncc_radius) ||
-        !sr::agg_supported(p.max_disp, p.agg_radius) || p.vol_dtype != SR_VOL_F32)
+        !sr::agg_supported(p.max_disp, p.agg_radius) ||
+        (p.vol_dtype != SR_VOL_F32 && p.vol_dtype != SR_VOL_F16 && p.vol_dtype != SR_VOL_BF16))
         return SR_ERR_UNSUPPORTED;
 
     // Carve the scratch: the same arrays sr_create allocates, 256-byte aligned.
     const size_t W = p.width, H = p.height, D = p.max_disp, npx = W * H, WE = W + D - 1;
     const size_t b_img = align256(npx * sizeof(float));
     const size_t b_ext = align256(H * WE * sizeof(float));
-    const size_t b_vol = align256(npx * D * sizeof(float));
+    const size_t b_vol = align256(npx * D * sr::vol_elem_bytes(p.vol_dtype));
     const size_t b_lbl = align256(npx * sizeof(int16_t));
     const size_t need = 2 * b_img + 4 * b_ext + 2 * b_vol + 2 * b_lbl;
     if (need > kSrNoallocScratchBytes) return SR_ERR_UNSUPPORTED;   // frame too large
@@ -96,8 +97,8 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     float *inv_l = reinterpret_cast<float *>(take(b_ext));
     float *mu_r = reinterpret_cast<float *>(take(b_ext));
     float *inv_r = reinterpret_cast<float *>(take(b_ext));
-    float *vol_l = reinterpret_cast<float *>(take(b_vol));
-    float *vol_r = reinterpret_cast<float *>(take(b_vol));
+    void *vol_l = take(b_vol);
+    void *vol_r = take(b_vol);
     int16_t *lbl_l = reinterpret_cast<int16_t *>(take(b_lbl));
     int16_t *lbl_r = reinterpret_cast<int16_t *>(take(b_lbl));
 
@@ -108,12 +109,12 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
         sr::launch_stats(d_left, pitch_bytes, rw, Wi, Hi, Di, p.ncc_radius, mu_l, inv_l, mu_r,
                          inv_r, st) != cudaSuccess ||
         sr::launch_ncc(false, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
-                       p.ncc_radius, vol_l, st) != cudaSuccess ||
+                       p.ncc_radius, vol_l, p.vol_dtype, st) != cudaSuccess ||
         sr::launch_ncc(true, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
-                       p.ncc_radius, vol_r, st) != cudaSuccess ||
-        sr::launch_agg(vol_l, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius, p.gamma_d,
+                       p.ncc_radius, vol_r, p.vol_dtype, st) != cudaSuccess ||
+        sr::launch_agg(vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius, p.gamma_d,
                        p.gamma_r, lbl_l, dsub, nullptr, dbg, st) != cudaSuccess ||
-        sr::launch_agg(vol_r, nullptr, 0, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d, p.gamma_r,
+        sr::launch_agg(vol_r, p.vol_dtype, nullptr, 0, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d, p.gamma_r,
                        lbl_r, nullptr, nullptr, dbg, st) != cudaSuccess ||
         sr::launch_lrc_post(lbl_l, lbl_r, dsub, Wi, Hi, alpha0, alpha1, delta, p.lr_thresh,
                             d_disp, d_wta_or_null, st) != cudaSuccess)

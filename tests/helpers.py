@@ -45,7 +45,7 @@ def oracle_params(w):
                          f_px=w.f_px, baseline=w.baseline_mm)
 
 
-def run_gpu(w, left, right, keep_agg=False, buffers=()):
+def run_gpu(w, left, right, keep_agg=False, buffers=(), vol_dtype=0):
     """Run sr_match (+ sr_reconstruct) on cuda:0 through the C ABI; return numpy arrays."""
     import torch
     from paper_1807_07433_gb300 import sr
@@ -54,7 +54,7 @@ def run_gpu(w, left, right, keep_agg=False, buffers=()):
     dr = torch.from_numpy(right).cuda()
     out = {}
     with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
-                    stream=torch.cuda.current_stream()) as m:
+                    vol_dtype=vol_dtype, stream=torch.cuda.current_stream()) as m:
         m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
         m.set_camera(w.f_px, w.baseline_mm)
         if keep_agg:

@@ -59,6 +59,7 @@ def test_status_strings(lib):
     ("gamma_r", float("nan"), "SR_ERR_INVALID_ARG"),
     ("lr_thresh", -1.0, "SR_ERR_INVALID_ARG"),
     ("vol_dtype", 7, "SR_ERR_INVALID_ARG"),
+    ("vol_dtype", -1, "SR_ERR_INVALID_ARG"),
     ("max_disp", 48, "SR_ERR_UNSUPPORTED"),
     ("max_disp", 128, "SR_ERR_UNSUPPORTED"),
     ("ncc_radius", 6, "SR_ERR_UNSUPPORTED"),
