@@ -394,6 +394,94 @@ def precision_report(steps: int, warmup: int):
             "steps": steps, "warmup": warmup, "forms": forms}
 
 
+def _gen_pair(scene):
+    from paper_1807_07433_gb300 import synth
+    left, right, _ = synth.make_pair(scene)
+    return left, right
+
+
+def batch_report(steps: int, warmup: int):
+    """Batched form on 64 mixed-size pairs (16 each of 672x376, 1280x720,
+    1920x1080, 2208x1242; D = 64, NCC 7x7, bilateral 11x11): one
+    sr_match_batch (persistent launches in a CUDA graph, autotuned) with FP32
+    and FP16 volumes, against 64 sequential plain FP32 sr_match calls (queued
+    back to back, and synchronised after each call)."""
+    import multiprocessing as mp
+
+    from paper_1807_07433_gb300 import synth
+    ws = synth.batch_workloads()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        data = pool.map(_gen_pair, [w.scene for w in ws])   # before any CUDA call
+
+    import torch
+    from paper_1807_07433_gb300 import sr
+    w0 = ws[0]
+    D = w0.D
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ins, outs = [], []
+    for (left, right) in data:
+        H, W = left.shape
+        ins.append((torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)))
+        outs.append(torch.empty((H, W), dtype=torch.float32, device=dev))
+    total_de = sum(w.scene.W * w.scene.H * D for w in ws)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    # 64 sequential plain FP32 calls, one context per image size
+    ctxs = {}
+    for w in ws:
+        key = (w.scene.W, w.scene.H)
+        if key not in ctxs:
+            ctxs[key] = sr.Matcher(w.scene.W, w.scene.H, D, w.ncc_r, w.agg_r, w.gamma_d,
+                                   w.gamma_r, w.lr_thresh, stream=stream)
+
+    def seq(sync):
+        for w, (dl, dr), out in zip(ws, ins, outs):
+            m = ctxs[(w.scene.W, w.scene.H)]
+            m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+            m.match(dl, dr, out)
+            if sync:
+                torch.cuda.synchronize()
+    for name, sync in (("sequential_f32_queued", False), ("sequential_f32_sync_each", True)):
+        t = timed(lambda: seq(sync))
+        res[name] = {"ms": round(t, 3), "mdes": round(total_de / (t * 1e-3) * 1e-6, 1)}
+    for m in ctxs.values():
+        m.close()
+
+    for name, vt in (("batched_f32", sr.SR_VOL_F32), ("batched_f16", sr.SR_VOL_F16)):
+        m = sr.Matcher(8, 8, D, w0.ncc_r, w0.agg_r, w0.gamma_d, w0.gamma_r, w0.lr_thresh,
+                       vol_dtype=vt, stream=stream)
+        sr.sr_set_autotune(m.ctx, True)
+        descs = [sr.make_pair_desc(dl, dr, out, w.scene.alpha0, w.scene.alpha1, w.delta)
+                 for w, (dl, dr), out in zip(ws, ins, outs)]
+        sr.sr_match_batch(m.ctx, descs)        # tunes on first use
+        torch.cuda.synchronize()
+        t = timed(lambda: sr.sr_match_batch(m.ctx, descs))
+        res[name] = {"ms": round(t, 3), "mdes": round(total_de / (t * 1e-3) * 1e-6, 1),
+                     "schedule": sr.sr_batch_info(m.ctx)}
+        m.close()
+        torch.cuda.empty_cache()
+    return {"report": "batch", "pairs": len(ws), "sizes": [list(s) for s in synth.BATCH_SIZES],
+            "D": D, "total_disparity_evaluations": total_de, "steps": steps, "warmup": warmup,
+            "l2": "flushed between timed steps", "forms": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,13 +489,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--report", choices=("precision",), default=None,
+    ap.add_argument("--report", choices=("precision", "batch"), default=None,
                     help="print a report instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.report == "precision":
         print(json.dumps(precision_report(args.steps, args.warmup)), flush=True)
+        return
+    if args.report == "batch":
+        print(json.dumps(batch_report(args.steps, args.warmup)), flush=True)
         return
     from paper_1807_07433_gb300 import synth
     w = synth.C2

@@ -156,6 +156,48 @@ sr_status sr_match_noalloc(const sr_params *params, double alpha0, double alpha1
                            const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                            float *d_disp, int16_t *d_wta_or_null, void *cuda_stream);
 
+/* One stereo pair of a batch (all pointers device pointers owned by the
+ * caller; layouts as for sr_match). */
+typedef struct {
+    int width, height;          /* 1..16384 each */
+    int pitch_bytes;            /* row pitch of both images, >= width */
+    const uint8_t *d_left, *d_right;
+    double alpha0, alpha1, delta;   /* Eq. 2 plane and offset of this pair */
+    float *d_disp;              /* width x height, dense */
+    int16_t *d_wta_or_null;     /* optional, width x height */
+} sr_pair_desc;
+
+/* The pipeline of sr_match for n pairs of any sizes in one call: each stage
+ * is one persistent launch over the flat list of (pair, tile) work items of
+ * the whole batch, and the seven stage launches are captured once into a CUDA
+ * graph that later calls replay.  The context supplies D, the radii, gamma_d,
+ * gamma_r, lr_thresh, vol_dtype and the stream; its width and height are not
+ * used.  Scratch for the whole batch (about sum of W*H*(2*D*e + 40) bytes,
+ * e as for sr_create) is allocated on first use and grown when a larger batch
+ * arrives.  Results are identical to n sr_match calls.  Asynchronous.
+ * Errors: SR_ERR_INVALID_ARG (n < 1, a bad pair), SR_ERR_OOM, SR_ERR_CUDA. */
+sr_status sr_match_batch(sr_ctx *ctx, int n, const sr_pair_desc *pairs);
+
+/* Autotuning of sr_match_batch.  With enable != 0, the first batch of each
+ * shape (multiset of image sizes, D, radii, volume type, GPU) times the
+ * candidate schedules -- grid factor 1 or 2 of the persistent NCC and
+ * aggregation launches, caller's pair order or largest pair first -- on the
+ * caller's data and keeps the fastest.  cache_path (nullable) names a file of
+ * one JSON object per line that stores the choices across processes;
+ * unreadable lines are skipped (defaults used) and reported by
+ * sr_last_error.  Disabled: grid factor 1, caller's order. */
+sr_status sr_set_autotune(sr_ctx *ctx, int enable, const char *cache_path);
+
+/* Fix the schedule of sr_match_batch instead of tuning it: 0-3 one
+ * persistent launch per stage (bit 0: two waves of CTAs instead of one;
+ * bit 1: largest pair first), 4 / 5 per-pair launches on 4 / 8 streams of
+ * the graph, largest pair first; -1 restores the automatic choice.
+ * SR_ERR_INVALID_ARG for other values. */
+sr_status sr_set_batch_schedule(sr_ctx *ctx, int variant);
+
+/* One-line JSON description of the schedule of the last sr_match_batch. */
+sr_status sr_batch_info(sr_ctx *ctx, char *buf, size_t size);
+
 /* 3-D reconstruction, Sec. II-D, for the left pixels of a full-disparity
  * map d_disp (W x H float, as written by sr_match).  d_xyz receives three
  * planes of W x H floats (X, then Y, then Z) in the camera frame of the

@@ -60,8 +60,11 @@ struct AggCfg {
     static constexpr size_t EPIB = (size_t)kAggPix * (D + 1) * sizeof(float);
     static constexpr size_t UNIONB = ((RINGSB > EPIB ? RINGSB : EPIB) + 15) / 16 * 16;
     static constexpr int GUIDE = TYE * TXE;
+    // (+ the batched kernel's work-list prefix and next-item slot, last, so
+    // that the cost ring at offset 0 keeps the alignment TMA copies prefer)
     static constexpr size_t SMEM = UNIONB + sizeof(float) * ((GUIDE + 3) / 4 * 4 + kAggPix) +
-                                   2 * sizeof(unsigned long long);
+                                   2 * sizeof(unsigned long long) +
+                                   sizeof(int) * (kStartSmem + 4);
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
 };
 
@@ -117,22 +120,50 @@ __device__ __forceinline__ float ex2_approx(float x) {   // 2^x, hardware approx
     return y;
 }
 
-template <int R, int D, bool GU8, typename VT>
-__global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
-k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
-          const float *__restrict__ gf, int W, int H, float kd, float kr,
-          int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
-          int *__restrict__ err, long long wait_cycles, int withhold_last) {
+// Shared-memory carve-up of an aggregation CTA (see AggCfg).
+template <int R, int D, typename VT>
+struct AggSmem {
     using C = AggCfg<R, D, VT>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *smem = reinterpret_cast<float *>(smem_raw);            // epilogue view
-    VT *ring = reinterpret_cast<VT *>(smem_raw);                  // [2][TXE][D] cost rows
-    float *wring = reinterpret_cast<float *>(smem_raw + C::RINGB);  // [2][4][WS][32] weights
-    float *guide = reinterpret_cast<float *>(smem_raw + C::UNIONB);  // [TYE][TXE]
-    float *wsum = guide + (C::GUIDE + 3) / 4 * 4;  // [128]
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(wsum + kAggPix);  // [2]
+    unsigned char *raw;
+    __device__ float *epi() const { return reinterpret_cast<float *>(raw); }
+    __device__ VT *ring() const { return reinterpret_cast<VT *>(raw); }
+    __device__ float *wring() const { return reinterpret_cast<float *>(raw + C::RINGB); }
+    __device__ float *guide() const { return reinterpret_cast<float *>(raw + C::UNIONB); }
+    __device__ float *wsum() const { return guide() + (C::GUIDE + 3) / 4 * 4; }
+    __device__ unsigned long long *bars() const {
+        return reinterpret_cast<unsigned long long *>(wsum() + kAggPix);
+    }
+    __device__ int *next_slot() const { return reinterpret_cast<int *>(bars() + 2); }
+    __device__ int *start() const { return next_slot() + 4; }
+};
 
-    const int x0 = blockIdx.x * kAggTX, y0 = blockIdx.y * kAggTY;
+template <int R, int D, typename VT>
+__device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT> &sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bars()[0], 1);
+        mbar_init(&sm.bars()[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+}
+
+// One 32 x 4 tile at (x0, y0) with all D disparities.  ph holds, per ring
+// slot, the parity of the slot's next mbarrier phase; it carries over from
+// tile to tile of a persistent CTA.  All threads of the CTA take part.
+template <int R, int D, bool GU8, typename VT>
+__device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &ph,
+                                         const VT *__restrict__ vol, const uint8_t *__restrict__ gl,
+                                         int pitch, const float *__restrict__ gf, int W, int H,
+                                         float kd, float kr, int16_t *__restrict__ lbl,
+                                         float *__restrict__ dsub, float *__restrict__ agg,
+                                         int *__restrict__ err, long long wait_cycles,
+                                         int withhold_last, int x0, int y0) {
+    using C = AggCfg<R, D, VT>;
+    float *smem = sm.epi();                      // epilogue view
+    VT *ring = sm.ring();                        // [2][TXE][D] cost rows
+    float *wring = sm.wring();                   // [2][4][WS][32] weights
+    float *guide = sm.guide();                   // [TYE][TXE]
+    float *wsum = sm.wsum();                     // [128]
+    unsigned long long *bars = sm.bars();        // [2]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // Columns of the tile's cost rows that lie inside the image; the rest of
@@ -193,12 +224,7 @@ k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
         }
     };
 
-    // ---- prologue: barriers, guide tile, zeroed columns, first row ----------
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
+    // ---- prologue: guide tile, zeroed columns, first row --------------------
     for (int i = tid; i < C::GUIDE; i += C::NT) {
         const int r = i / C::TXE, c = i % C::TXE;
         const int y = y0 - R + r, x = x0 - R + c;
@@ -244,7 +270,7 @@ k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
         }
         const int y = y0 - R + j;
         if (y >= 0 && y < H) {
-            mbar_wait(bars + (j & 1), (unsigned)((j >> 1) & 1), wait_cycles, err);
+            mbar_wait(bars + (j & 1), (ph >> (j & 1)) & 1u, wait_cycles, err);
             const VT *rs = ring + (j & 1) * C::RING + bx * D + 2 * sl;
             const float *ws = wring + (j & 1) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
@@ -270,6 +296,7 @@ k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
                 }
             }
         }
+        ph ^= 1u << (j & 1);   // every source row completes one phase of its slot
         __syncthreads();
     }
 
@@ -327,6 +354,57 @@ k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
     }
 }
 
+template <int R, int D, bool GU8, typename VT>
+__global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
+k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
+          const float *__restrict__ gf, int W, int H, float kd, float kr,
+          int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
+          int *__restrict__ err, long long wait_cycles, int withhold_last) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const AggSmem<R, D, VT> sm{smem_raw};
+    agg_init_barriers(sm);
+    unsigned ph = 0;
+    agg_tile<R, D, GU8, VT>(sm, ph, vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, err,
+                            wait_cycles, withhold_last, blockIdx.x * kAggTX, blockIdx.y * kAggTY);
+}
+
+// Persistent batched form: CTA b handles work items b, b + gridDim.x, ... of
+// the batch's flat (pair, tile) list.  TARGET selects the target volume
+// (guide = warped target, no subpixel map) or the reference volume.
+template <int R, int D, bool TARGET, typename VT>
+__global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
+k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, int n, float kd,
+            float kr, int *__restrict__ err, long long wait_cycles, int *__restrict__ next) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const AggSmem<R, D, VT> sm{smem_raw};
+    agg_init_barriers(sm);
+    int &s_t = *sm.next_slot();
+    const int *st = stage_start(sm.start(), start, n);
+    unsigned ph = 0;
+    const int total = st[n];
+    int p = 0;
+    for (int t = blockIdx.x;; ) {
+        // next work item: in order from a counter (keeps the tiles in flight a
+        // contiguous band, so halo rows are shared through L2), or strided
+        __syncthreads();   // the previous tile's epilogue is done with shared memory
+        if (next) {
+            if (threadIdx.x == 0) s_t = atomicAdd(next, 1);
+            __syncthreads();
+            t = s_t;
+        }
+        if (t >= total) break;
+        p = find_pair(st, n, t, p);
+        const PairDesc &P = pairs[p];
+        const int tl = t - st[p], tx = (P.W + kAggTX - 1) / kAggTX;
+        agg_tile<R, D, !TARGET, VT>(sm, ph, static_cast<const VT *>(TARGET ? P.vol_r : P.vol_l),
+                                    TARGET ? nullptr : P.left, P.pitch, TARGET ? P.rw : nullptr,
+                                    P.W, P.H, kd, kr, TARGET ? P.lbl_r : P.lbl_l,
+                                    TARGET ? nullptr : P.dsub, nullptr, err, wait_cycles, 0,
+                                    (tl % tx) * kAggTX, (tl / tx) * kAggTY);
+        if (!next) t += gridDim.x;
+    }
+}
+
 template <int R, int D, typename VT>
 cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
@@ -341,20 +419,61 @@ cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const floa
     return cudaGetLastError();
 }
 
+template <int R, int D, typename VT>
+cudaError_t agg_batch_t(bool target, const PairDesc *pairs, const int *start, int n, float kd,
+                        float kr, const AggDebug &dbg, int grid, int *next, cudaStream_t st) {
+    using C = AggCfg<R, D, VT>;
+    auto k = target ? k_agg_batch<R, D, true, VT> : k_agg_batch<R, D, false, VT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    k<<<grid, C::NT, C::SMEM, st>>>(pairs, start, n, kd, kr, dbg.err, dbg.wait_cycles, next);
+    return cudaGetLastError();
+}
+
+template <int R, int D, typename VT>
+int agg_occ_t() {
+    using C = AggCfg<R, D, VT>;
+    int b = 0;
+    cudaFuncSetAttribute(k_agg_batch<R, D, false, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_agg_batch<R, D, false, VT>, C::NT, C::SMEM);
+    return b;
+}
+
+#define SR_AGG_R_SWITCH(agg_r, CALL)                 \
+    switch (agg_r) {                                 \
+        case 1: { constexpr int R_ = 1; CALL; }      \
+        case 2: { constexpr int R_ = 2; CALL; }      \
+        case 3: { constexpr int R_ = 3; CALL; }      \
+        case 4: { constexpr int R_ = 4; CALL; }      \
+        case 5: { constexpr int R_ = 5; CALL; }      \
+        case 6: { constexpr int R_ = 6; CALL; }      \
+        case 7: { constexpr int R_ = 7; CALL; }      \
+        default: break;                              \
+    }
+
 template <int D, typename VT>
 cudaError_t agg_launch_d(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub,
                          float *agg, const AggDebug &dbg, cudaStream_t st) {
-    switch (agg_r) {
-        case 1: return agg_launch_t<1, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 2: return agg_launch_t<2, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 3: return agg_launch_t<3, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 4: return agg_launch_t<4, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 5: return agg_launch_t<5, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 6: return agg_launch_t<6, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        case 7: return agg_launch_t<7, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg, st);
-        default: return cudaErrorInvalidValue;
-    }
+    SR_AGG_R_SWITCH(agg_r, return (agg_launch_t<R_, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl,
+                                                           dsub, agg, dbg, st)))
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename VT>
+cudaError_t agg_batch_d(bool target, const PairDesc *pairs, const int *start, int n, int agg_r,
+                        float kd, float kr, const AggDebug &dbg, int grid, int *next,
+                        cudaStream_t st) {
+    SR_AGG_R_SWITCH(agg_r, return (agg_batch_t<R_, D, VT>(target, pairs, start, n, kd, kr, dbg,
+                                                          grid, next, st)))
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename VT>
+int agg_occ_d(int agg_r) {
+    SR_AGG_R_SWITCH(agg_r, return (agg_occ_t<R_, D, VT>()))
+    return 0;
 }
 
 }  // namespace sr

@@ -6,4 +6,10 @@ cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, co
     return agg_launch_d<64, __half>(static_cast<const __half *>(vol), gl, pitch, gf, W, H, agg_r, kd, kr,
                                    lbl, dsub, agg, dbg, st);
 }
+cudaError_t launch_agg_batch_d64_f16(bool target, const PairDesc *pairs, const int *start, int n,
+                                  int agg_r, float kd, float kr, const AggDebug &dbg, int grid,
+                                  int *next, cudaStream_t st) {
+    return agg_batch_d<64, __half>(target, pairs, start, n, agg_r, kd, kr, dbg, grid, next, st);
+}
+int agg_occ_d64_f16(int agg_r) { return agg_occ_d<64, __half>(agg_r); }
 }  // namespace sr

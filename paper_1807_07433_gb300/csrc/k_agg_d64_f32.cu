@@ -6,4 +6,10 @@ cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, co
     return agg_launch_d<64, float>(static_cast<const float *>(vol), gl, pitch, gf, W, H, agg_r, kd, kr,
                                    lbl, dsub, agg, dbg, st);
 }
+cudaError_t launch_agg_batch_d64_f32(bool target, const PairDesc *pairs, const int *start, int n,
+                                  int agg_r, float kd, float kr, const AggDebug &dbg, int grid,
+                                  int *next, cudaStream_t st) {
+    return agg_batch_d<64, float>(target, pairs, start, n, agg_r, kd, kr, dbg, grid, next, st);
+}
+int agg_occ_d64_f32(int agg_r) { return agg_occ_d<64, float>(agg_r); }
 }  // namespace sr

@@ -28,6 +28,9 @@
 // Tiles: 32 x 4 output pixels per CTA (128 threads); the fixed image tile and
 // the sliding image tile (widened by D-1 columns) are staged in shared memory
 // with clamp-to-edge reads, as the block definition of Eqs. 3-5 requires.
+// The per-tile work is one device function, used by the single-image kernel
+// (one tile per CTA) and by the batched kernel (a persistent CTA walks the
+// flat (pair, tile) list of a batch).
 #pragma once
 #include "sr_internal.cuh"
 
@@ -35,24 +38,31 @@ namespace sr {
 
 constexpr int kNccTX = 32, kNccTY = 4, kNccThreads = kNccTX * kNccTY;
 
-template <int RN, int D, bool TARGET, typename VT>
-__global__ void __launch_bounds__(kNccThreads)
-k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
-      const float *__restrict__ mu_l, const float *__restrict__ inv_l,
-      const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
-      VT *__restrict__ vol) {
-    constexpr int B = 2 * RN + 1;
-    constexpr int FW = kNccTX + 2 * RN;          // fixed tile width
-    constexpr int SW = kNccTX + 2 * RN + D - 1;  // sliding tile width
-    constexpr int TH = kNccTY + 2 * RN;          // tile height
-    constexpr int DC = D < 32 ? D : 32;          // disparity chunk held in registers
-    constexpr int XW = kNccTX + D - 1;           // sliding-block centres per tile row
-    __shared__ float fix_s[TH][FW];
-    __shared__ float sld_s[TH][SW];
-    __shared__ float smu_s[kNccTY][XW];          // sliding-block mean
-    __shared__ float sinv_s[kNccTY][XW];         // sliding-block 1/(n sigma)
+template <int RN, int D>
+struct NccSmem {
+    static constexpr int B = 2 * RN + 1;
+    static constexpr int FW = kNccTX + 2 * RN;          // fixed tile width
+    static constexpr int SW = kNccTX + 2 * RN + D - 1;  // sliding tile width
+    static constexpr int TH = kNccTY + 2 * RN;          // tile height
+    static constexpr int XW = kNccTX + D - 1;           // sliding-block centres per tile row
+    float fix_s[TH][FW];
+    float sld_s[TH][SW];
+    float smu_s[kNccTY][XW];                            // sliding-block mean
+    float sinv_s[kNccTY][XW];                           // sliding-block 1/(n sigma)
+};
 
-    const int x0 = blockIdx.x * kNccTX, y0 = blockIdx.y * kNccTY;
+// One 32 x 4 tile at (x0, y0).  All threads of the CTA take part (barrier).
+template <int RN, int D, bool TARGET, typename VT>
+__device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__restrict__ left,
+                                         int pitch, const float *__restrict__ rw,
+                                         const float *__restrict__ mu_l,
+                                         const float *__restrict__ inv_l,
+                                         const float *__restrict__ mu_r,
+                                         const float *__restrict__ inv_r, int W, int H,
+                                         VT *__restrict__ vol, int x0, int y0) {
+    using S = NccSmem<RN, D>;
+    constexpr int B = S::B, FW = S::FW, SW = S::SW, TH = S::TH, XW = S::XW;
+    constexpr int DC = D < 32 ? D : 32;          // disparity chunk held in registers
     const int tid = threadIdx.x;
     const int WE = W + D - 1;
 
@@ -62,13 +72,13 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     for (int i = tid; i < TH * FW; i += kNccThreads) {
         const int r = i / FW, c = i % FW;
         const int y = clampi(y0 - RN + r, 0, H - 1), x = clampi(fx0 + c, 0, W - 1);
-        fix_s[r][c] = TARGET ? rw[(size_t)y * W + x] : (float)left[(size_t)y * pitch + x];
+        sm.fix_s[r][c] = TARGET ? rw[(size_t)y * W + x] : (float)left[(size_t)y * pitch + x];
     }
     for (int i = tid; i < TH * SW; i += kNccThreads) {
         const int r = i / SW, c = i % SW;
         const int y = clampi(y0 - RN + r, 0, H - 1), x = clampi(sx0 + c, 0, W - 1);
         const float val = TARGET ? (float)left[(size_t)y * pitch + x] : rw[(size_t)y * W + x];
-        sld_s[r][c] = val - kNccOffset;
+        sm.sld_s[r][c] = val - kNccOffset;
     }
     // Sliding-block statistics of the tile's rows.  In the extended stats rows
     // (see launch_stats) the centres u-d (reference) and u+d (target) of the
@@ -80,8 +90,8 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
             const int r = i / XW, t = i % XW;
             const int y = clampi(y0 + r, 0, H - 1);
             const int xi = clampi(x0 + t, 0, WE - 1);
-            smu_s[r][t] = mu_s[(size_t)y * WE + xi];
-            sinv_s[r][t] = inv_s[(size_t)y * WE + xi];
+            sm.smu_s[r][t] = mu_s[(size_t)y * WE + xi];
+            sm.sinv_s[r][t] = inv_s[(size_t)y * WE + xi];
         }
     }
     __syncthreads();
@@ -96,8 +106,8 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     const float *mu_f = TARGET ? mu_r + rowo + u + D - 1 : mu_l + rowo + u;
     const float *inv_fp = TARGET ? inv_r + rowo + u + D - 1 : inv_l + rowo + u;
     // sliding centre of disparity d at smem index base + so, so = d or -d
-    const float *mu_s_row = &smu_s[ty][TARGET ? tx : tx + D - 1];
-    const float *inv_s_row = &sinv_s[ty][TARGET ? tx : tx + D - 1];
+    const float *mu_s_row = &sm.smu_s[ty][TARGET ? tx : tx + D - 1];
+    const float *inv_s_row = &sm.sinv_s[ty][TARGET ? tx : tx + D - 1];
 
     // Centred fixed block and the sum of its (rounded) centred values.
     const float m = *mu_f;
@@ -107,7 +117,7 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     for (int oy = 0; oy < B; ++oy)
 #pragma unroll
         for (int ox = 0; ox < B; ++ox) {
-            a[oy][ox] = fix_s[ty + oy][tx + ox] - m;
+            a[oy][ox] = sm.fix_s[ty + oy][tx + ox] - m;
             sa += a[oy][ox];
         }
 
@@ -129,7 +139,7 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
             const int sc = TARGET ? tx + k + RN : tx - k + RN + D - 1;
             float col[B];
 #pragma unroll
-            for (int oy = 0; oy < B; ++oy) col[oy] = sld_s[ty + oy][sc];
+            for (int oy = 0; oy < B; ++oy) col[oy] = sm.sld_s[ty + oy][sc];
 #pragma unroll
             for (int ox = 0; ox < B; ++ox) {
                 const int dl = TARGET ? kk - ox : kk + ox - 2 * RN;   // d - d0
@@ -155,6 +165,46 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
     }
 }
 
+template <int RN, int D, bool TARGET, typename VT>
+__global__ void __launch_bounds__(kNccThreads)
+k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
+      const float *__restrict__ mu_l, const float *__restrict__ inv_l,
+      const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
+      VT *__restrict__ vol) {
+    __shared__ NccSmem<RN, D> sm;
+    ncc_tile<RN, D, TARGET, VT>(sm, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol,
+                                blockIdx.x * kNccTX, blockIdx.y * kNccTY);
+}
+
+// Persistent batched form: CTA b handles work items b, b + gridDim.x, ...
+template <int RN, int D, bool TARGET, typename VT>
+__global__ void __launch_bounds__(kNccThreads)
+k_ncc_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, int n,
+            int *__restrict__ next) {
+    __shared__ NccSmem<RN, D> sm;
+    __shared__ int s_start[kStartSmem];
+    __shared__ int s_t;
+    const int *st = stage_start(s_start, start, n);
+    const int total = st[n];
+    int p = 0;
+    for (int t = blockIdx.x;; ) {
+        __syncthreads();   // the previous tile is done with shared memory
+        if (next) {        // in-order work items from a counter, else strided
+            if (threadIdx.x == 0) s_t = atomicAdd(next, 1);
+            __syncthreads();
+            t = s_t;
+        }
+        if (t >= total) break;
+        p = find_pair(st, n, t, p);
+        const PairDesc &P = pairs[p];
+        const int tl = t - st[p], tx = (P.W + kNccTX - 1) / kNccTX;
+        ncc_tile<RN, D, TARGET, VT>(sm, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r,
+                                    P.W, P.H, static_cast<VT *>(TARGET ? P.vol_r : P.vol_l),
+                                    (tl % tx) * kNccTX, (tl / tx) * kNccTY);
+        if (!next) t += gridDim.x;
+    }
+}
+
 template <int RN, int D, typename VT>
 cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
@@ -167,19 +217,54 @@ cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const floa
     return cudaGetLastError();
 }
 
+template <int RN, int D, typename VT>
+cudaError_t ncc_batch_t(bool target, const PairDesc *pairs, const int *start, int n, int grid,
+                        int *next, cudaStream_t st) {
+    if (target)
+        k_ncc_batch<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(pairs, start, n, next);
+    else
+        k_ncc_batch<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(pairs, start, n, next);
+    return cudaGetLastError();
+}
+
+template <int RN, int D, typename VT>
+int ncc_occ_t() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ncc_batch<RN, D, false, VT>, kNccThreads, 0);
+    return b;
+}
+
+#define SR_NCC_RN_SWITCH(ncc_r, CALL)                \
+    switch (ncc_r) {                                 \
+        case 1: { constexpr int RN_ = 1; CALL; }     \
+        case 2: { constexpr int RN_ = 2; CALL; }     \
+        case 3: { constexpr int RN_ = 3; CALL; }     \
+        case 4: { constexpr int RN_ = 4; CALL; }     \
+        case 5: { constexpr int RN_ = 5; CALL; }     \
+        default: break;                              \
+    }
+
 template <int D, typename VT>
 cudaError_t ncc_launch_d(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
                          const float *inv_r, int W, int H, int ncc_r, VT *vol,
                          cudaStream_t st) {
-    switch (ncc_r) {
-        case 1: return ncc_launch_t<1, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 2: return ncc_launch_t<2, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 3: return ncc_launch_t<3, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 4: return ncc_launch_t<4, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        case 5: return ncc_launch_t<5, D, VT>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, st);
-        default: return cudaErrorInvalidValue;
-    }
+    SR_NCC_RN_SWITCH(ncc_r, return (ncc_launch_t<RN_, D, VT>(target, left, pitch, rw, mu_l, inv_l,
+                                                             mu_r, inv_r, W, H, vol, st)))
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename VT>
+cudaError_t ncc_batch_d(bool target, const PairDesc *pairs, const int *start, int n, int ncc_r,
+                        int grid, int *next, cudaStream_t st) {
+    SR_NCC_RN_SWITCH(ncc_r, return (ncc_batch_t<RN_, D, VT>(target, pairs, start, n, grid, next, st)))
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename VT>
+int ncc_occ_d(int ncc_r) {
+    SR_NCC_RN_SWITCH(ncc_r, return (ncc_occ_t<RN_, D, VT>()))
+    return 0;
 }
 
 }  // namespace sr

@@ -6,4 +6,9 @@ cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, con
     return ncc_launch_d<32, __nv_bfloat16>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r,
                                    static_cast<__nv_bfloat16 *>(vol), st);
 }
+cudaError_t launch_ncc_batch_d32_bf16(bool target, const PairDesc *pairs, const int *start, int n,
+                                  int ncc_r, int grid, int *next, cudaStream_t st) {
+    return ncc_batch_d<32, __nv_bfloat16>(target, pairs, start, n, ncc_r, grid, next, st);
+}
+int ncc_occ_d32_bf16(int ncc_r) { return ncc_occ_d<32, __nv_bfloat16>(ncc_r); }
 }  // namespace sr

@@ -6,4 +6,9 @@ cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, cons
     return ncc_launch_d<32, __half>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r,
                                    static_cast<__half *>(vol), st);
 }
+cudaError_t launch_ncc_batch_d32_f16(bool target, const PairDesc *pairs, const int *start, int n,
+                                  int ncc_r, int grid, int *next, cudaStream_t st) {
+    return ncc_batch_d<32, __half>(target, pairs, start, n, ncc_r, grid, next, st);
+}
+int ncc_occ_d32_f16(int ncc_r) { return ncc_occ_d<32, __half>(ncc_r); }
 }  // namespace sr

@@ -10,13 +10,11 @@
 namespace sr {
 namespace {
 
-constexpr int kBX = 32, kBY = 8;
+constexpr int kBX = kPixTX, kBY = kPixTY;
 
-__global__ void k_warp(const uint8_t *__restrict__ right, int pitch, int W, int H, double alpha0,
-                       double alpha1, double delta, float *__restrict__ rw) {
-    const int x = blockIdx.x * kBX + threadIdx.x;
-    const int v = blockIdx.y * kBY + threadIdx.y;
-    if (x >= W || v >= H) return;
+__device__ __forceinline__ void warp_px(const uint8_t *__restrict__ right, int pitch, int W,
+                                        double alpha0, double alpha1, double delta,
+                                        float *__restrict__ rw, int x, int v) {
     // s(v) of Sec. II-A in double: it also feeds Sec. II-C post-processing.
     const double s = alpha0 + alpha1 * (double)v - delta;
     double k = floor(s);
@@ -29,14 +27,20 @@ __global__ void k_warp(const uint8_t *__restrict__ right, int pitch, int W, int 
     rw[(size_t)v * W + x] = fmaf(w, b - a, a);        // (1-w) a + w b
 }
 
+__global__ void k_warp(const uint8_t *__restrict__ right, int pitch, int W, int H, double alpha0,
+                       double alpha1, double delta, float *__restrict__ rw) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (x >= W || v >= H) return;
+    warp_px(right, pitch, W, alpha0, alpha1, delta, rw, x, v);
+}
+
 // Left block statistics from exact integer sums: n^2 sigma^2 = n S2 - S^2.
 // Centres x in [0, W+D-1) (the target volume needs left blocks at u+d).
 template <int RN>
-__global__ void k_stats_left(const uint8_t *__restrict__ left, int pitch, int W, int H, int WE,
-                             float *__restrict__ mu, float *__restrict__ inv) {
-    const int x = blockIdx.x * kBX + threadIdx.x;
-    const int v = blockIdx.y * kBY + threadIdx.y;
-    if (x >= WE || v >= H) return;
+__device__ __forceinline__ void stats_left_px(const uint8_t *__restrict__ left, int pitch, int W,
+                                              int H, int WE, float *__restrict__ mu,
+                                              float *__restrict__ inv, int x, int v) {
     constexpr int n = (2 * RN + 1) * (2 * RN + 1);
     unsigned s = 0, s2 = 0;
 #pragma unroll
@@ -55,14 +59,19 @@ __global__ void k_stats_left(const uint8_t *__restrict__ left, int pitch, int W,
     mu[(size_t)v * WE + x] = (float)s / (float)n;
 }
 
-// Warped-target block statistics, two-pass (mean, then centred squares).
-// Centres x in [-(D-1), W), stored at x + D - 1.
 template <int RN>
-__global__ void k_stats_right(const float *__restrict__ rw, int W, int H, int D, int WE,
-                              float *__restrict__ mu, float *__restrict__ inv) {
-    const int xi = blockIdx.x * kBX + threadIdx.x;
+__global__ void k_stats_left(const uint8_t *__restrict__ left, int pitch, int W, int H, int WE,
+                             float *__restrict__ mu, float *__restrict__ inv) {
+    const int x = blockIdx.x * kBX + threadIdx.x;
     const int v = blockIdx.y * kBY + threadIdx.y;
-    if (xi >= WE || v >= H) return;
+    if (x >= WE || v >= H) return;
+    stats_left_px<RN>(left, pitch, W, H, WE, mu, inv, x, v);
+}
+
+template <int RN>
+__device__ __forceinline__ void stats_right_px(const float *__restrict__ rw, int W, int H, int D,
+                                               int WE, float *__restrict__ mu,
+                                               float *__restrict__ inv, int xi, int v) {
     const int x = xi - (D - 1);
     constexpr int n = (2 * RN + 1) * (2 * RN + 1);
     // Mean: row sums of (value - 128) then their sum, so that no partial sum
@@ -94,13 +103,23 @@ __global__ void k_stats_right(const float *__restrict__ rw, int W, int H, int D,
     mu[(size_t)v * WE + xi] = m;
 }
 
-__global__ void k_lrc_post(const int16_t *__restrict__ lbl_l, const int16_t *__restrict__ lbl_r,
-                           const float *__restrict__ dsub, int W, int H, double alpha0,
-                           double alpha1, double delta, float lr_thresh, float *__restrict__ disp,
-                           int16_t *__restrict__ wta_out) {
-    const int u = blockIdx.x * kBX + threadIdx.x;
+// Warped-target block statistics, two-pass (mean, then centred squares).
+// Centres x in [-(D-1), W), stored at x + D - 1.
+template <int RN>
+__global__ void k_stats_right(const float *__restrict__ rw, int W, int H, int D, int WE,
+                              float *__restrict__ mu, float *__restrict__ inv) {
+    const int xi = blockIdx.x * kBX + threadIdx.x;
     const int v = blockIdx.y * kBY + threadIdx.y;
-    if (u >= W || v >= H) return;
+    if (xi >= WE || v >= H) return;
+    stats_right_px<RN>(rw, W, H, D, WE, mu, inv, xi, v);
+}
+
+__device__ __forceinline__ void lrc_px(const int16_t *__restrict__ lbl_l,
+                                       const int16_t *__restrict__ lbl_r,
+                                       const float *__restrict__ dsub, int W, double alpha0,
+                                       double alpha1, double delta, float lr_thresh,
+                                       float *__restrict__ disp, int16_t *__restrict__ wta_out,
+                                       int u, int v) {
     const size_t i = (size_t)v * W + u;
     const int l = lbl_l[i];
     const int ur = u - l;
@@ -109,6 +128,76 @@ __global__ void k_lrc_post(const int16_t *__restrict__ lbl_l, const int16_t *__r
     const double s = alpha0 + alpha1 * (double)v - delta;
     disp[i] = ok ? (float)((double)dsub[i] + s) : __int_as_float(0x7fc00000);
     if (wta_out) wta_out[i] = (int16_t)l;
+}
+
+__global__ void k_lrc_post(const int16_t *__restrict__ lbl_l, const int16_t *__restrict__ lbl_r,
+                           const float *__restrict__ dsub, int W, int H, double alpha0,
+                           double alpha1, double delta, float lr_thresh, float *__restrict__ disp,
+                           int16_t *__restrict__ wta_out) {
+    const int u = blockIdx.x * kBX + threadIdx.x;
+    const int v = blockIdx.y * kBY + threadIdx.y;
+    if (u >= W || v >= H) return;
+    lrc_px(lbl_l, lbl_r, dsub, W, alpha0, alpha1, delta, lr_thresh, disp, wta_out, u, v);
+}
+
+// ---- batched forms: persistent 32x8 blocks over a batch's flat tile list --
+// Tile t of pair p covers columns [tx*32, tx*32+32) of the stage's width
+// (W, or W + D - 1 for the statistics) and rows [ty*8, ty*8+8).
+__device__ __forceinline__ bool batch_pixel(const PairDesc *pairs, const int *start, int n, int t,
+                                            int extra_w, const PairDesc **P, int *x, int *v,
+                                            int *pp) {
+    const int p = find_pair(start, n, t, *pp);
+    *pp = p;
+    *P = &pairs[p];
+    const int w = (*P)->W + extra_w;
+    const int tl = t - start[p], tx = (w + kBX - 1) / kBX;
+    *x = (tl % tx) * kBX + threadIdx.x;
+    *v = (tl / tx) * kBY + threadIdx.y;
+    return *x < w && *v < (*P)->H;
+}
+
+__global__ void k_warp_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start,
+                             int n) {
+    __shared__ int s_start[kStartSmem];
+    const int *st = stage_start(s_start, start, n);
+    int pp = 0;
+    for (int t = blockIdx.x; t < st[n]; t += gridDim.x) {
+        const PairDesc *P;
+        int x, v;
+        if (batch_pixel(pairs, st, n, t, 0, &P, &x, &v, &pp))
+            warp_px(P->right, P->pitch, P->W, P->alpha0, P->alpha1, P->delta, P->rw, x, v);
+    }
+}
+
+template <int RN>
+__global__ void k_stats_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start,
+                              int n, int D) {
+    __shared__ int s_start[kStartSmem];
+    const int *st = stage_start(s_start, start, n);
+    int pp = 0;
+    for (int t = blockIdx.x; t < st[n]; t += gridDim.x) {
+        const PairDesc *P;
+        int x, v;
+        if (batch_pixel(pairs, st, n, t, D - 1, &P, &x, &v, &pp)) {
+            const int WE = P->W + D - 1;
+            stats_left_px<RN>(P->left, P->pitch, P->W, P->H, WE, P->mu_l, P->inv_l, x, v);
+            stats_right_px<RN>(P->rw, P->W, P->H, D, WE, P->mu_r, P->inv_r, x, v);
+        }
+    }
+}
+
+__global__ void k_lrc_post_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start,
+                                 int n, float lr_thresh) {
+    __shared__ int s_start[kStartSmem];
+    const int *st = stage_start(s_start, start, n);
+    int pp = 0;
+    for (int t = blockIdx.x; t < st[n]; t += gridDim.x) {
+        const PairDesc *P;
+        int x, v;
+        if (batch_pixel(pairs, st, n, t, 0, &P, &x, &v, &pp))
+            lrc_px(P->lbl_l, P->lbl_r, P->dsub, P->W, P->alpha0, P->alpha1, P->delta, lr_thresh,
+                   P->disp, P->wta, x, v);
+    }
 }
 
 __global__ void k_xyz(const float *__restrict__ disp, int W, int H, float f, float fb, float u0,
@@ -168,6 +257,31 @@ cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const fl
                             float *disp, int16_t *wta_out, cudaStream_t st) {
     k_lrc_post<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(lbl_l, lbl_r, dsub, W, H, alpha0, alpha1,
                                                          delta, lr_thresh, disp, wta_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_batch(const PairDesc *pairs, const int *start, int n, int grid,
+                              cudaStream_t st) {
+    k_warp_batch<<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_batch(const PairDesc *pairs, const int *start, int n, int D, int ncc_r,
+                               int grid, cudaStream_t st) {
+    switch (ncc_r) {
+        case 1: k_stats_batch<1><<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, D); break;
+        case 2: k_stats_batch<2><<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, D); break;
+        case 3: k_stats_batch<3><<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, D); break;
+        case 4: k_stats_batch<4><<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, D); break;
+        case 5: k_stats_batch<5><<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, D); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lrc_post_batch(const PairDesc *pairs, const int *start, int n, float lr_thresh,
+                                  int grid, cudaStream_t st) {
+    k_lrc_post_batch<<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, lr_thresh);
     return cudaGetLastError();
 }
 

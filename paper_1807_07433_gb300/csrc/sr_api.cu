@@ -8,7 +8,7 @@
 #include <new>
 
 #include "../../include/sr.h"
-#include "sr_internal.cuh"
+#include "sr_ctx.cuh"
 
 namespace sr {
 cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
@@ -29,6 +29,43 @@ cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, cons
 cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
 cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
 cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+
+cudaError_t launch_ncc_batch_d16_f32(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d16_f32(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d16_f32(int);
+int agg_occ_d16_f32(int);
+cudaError_t launch_ncc_batch_d16_f16(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d16_f16(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d16_f16(int);
+int agg_occ_d16_f16(int);
+cudaError_t launch_ncc_batch_d16_bf16(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d16_bf16(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d16_bf16(int);
+int agg_occ_d16_bf16(int);
+cudaError_t launch_ncc_batch_d32_f32(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d32_f32(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d32_f32(int);
+int agg_occ_d32_f32(int);
+cudaError_t launch_ncc_batch_d32_f16(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d32_f16(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d32_f16(int);
+int agg_occ_d32_f16(int);
+cudaError_t launch_ncc_batch_d32_bf16(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d32_bf16(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d32_bf16(int);
+int agg_occ_d32_bf16(int);
+cudaError_t launch_ncc_batch_d64_f32(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d64_f32(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d64_f32(int);
+int agg_occ_d64_f32(int);
+cudaError_t launch_ncc_batch_d64_f16(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d64_f16(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d64_f16(int);
+int agg_occ_d64_f16(int);
+cudaError_t launch_ncc_batch_d64_bf16(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
+cudaError_t launch_agg_batch_d64_bf16(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
+int ncc_occ_d64_bf16(int);
+int agg_occ_d64_bf16(int);
 
 bool ncc_supported(int D, int ncc_r) {
     return (D == 16 || D == 32 || D == 64) && ncc_r >= 1 && ncc_r <= 5;
@@ -71,50 +108,65 @@ cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pit
     }
 }
 
+cudaError_t launch_ncc_batch(bool target, const PairDesc *pairs, const int *start, int n, int D,
+                             int ncc_r, int vt, int grid, int *next, cudaStream_t st) {
+    switch (D) {
+        case 16: SR_VT_DISPATCH(launch_ncc_batch, 16, vt, target, pairs, start, n, ncc_r, grid, next, st)
+        case 32: SR_VT_DISPATCH(launch_ncc_batch, 32, vt, target, pairs, start, n, ncc_r, grid, next, st)
+        case 64: SR_VT_DISPATCH(launch_ncc_batch, 64, vt, target, pairs, start, n, ncc_r, grid, next, st)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_agg_batch(bool target, const PairDesc *pairs, const int *start, int n, int D,
+                             int agg_r, int vt, float gamma_d, float gamma_r, const AggDebug &dbg,
+                             int grid, int *next, cudaStream_t st) {
+    const float log2e = 1.4426950408889634f;
+    const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
+    switch (D) {
+        case 16: SR_VT_DISPATCH(launch_agg_batch, 16, vt, target, pairs, start, n, agg_r, kd, kr, dbg, grid, next, st)
+        case 32: SR_VT_DISPATCH(launch_agg_batch, 32, vt, target, pairs, start, n, agg_r, kd, kr, dbg, grid, next, st)
+        case 64: SR_VT_DISPATCH(launch_agg_batch, 64, vt, target, pairs, start, n, agg_r, kd, kr, dbg, grid, next, st)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+#define SR_OCC_DISPATCH(FN, D, vt, r)                     \
+    switch (vt) {                                         \
+        case kVolF32: return FN##_d##D##_f32(r);          \
+        case kVolF16: return FN##_d##D##_f16(r);          \
+        case kVolBF16: return FN##_d##D##_bf16(r);        \
+        default: return 0;                                \
+    }
+
+int ncc_batch_occupancy(int D, int ncc_r, int vt) {
+    switch (D) {
+        case 16: SR_OCC_DISPATCH(ncc_occ, 16, vt, ncc_r)
+        case 32: SR_OCC_DISPATCH(ncc_occ, 32, vt, ncc_r)
+        case 64: SR_OCC_DISPATCH(ncc_occ, 64, vt, ncc_r)
+        default: return 0;
+    }
+}
+
+int agg_batch_occupancy(int D, int agg_r, int vt) {
+    switch (D) {
+        case 16: SR_OCC_DISPATCH(agg_occ, 16, vt, agg_r)
+        case 32: SR_OCC_DISPATCH(agg_occ, 32, vt, agg_r)
+        case 64: SR_OCC_DISPATCH(agg_occ, 64, vt, agg_r)
+        default: return 0;
+    }
+}
+
 }  // namespace sr
 
 namespace {
 
-constexpr int kStages = 7;
 const char *const kStageNames = "warp,stats,ncc_ref,ncc_tgt,agg_ref,agg_tgt,lrc_post";
 
 }  // namespace
 
-struct sr_ctx {
-    sr_params p{};
-    cudaStream_t st = nullptr;
-    int device = 0;
-    double alpha0 = 0, alpha1 = 0, delta = 0;
-    double f_px = 0, baseline = 0, u0 = 0, v0 = 0;
-    bool camera = false;
-    // scratch (owned)
-    float *rw = nullptr, *mu_l = nullptr, *inv_l = nullptr, *mu_r = nullptr, *inv_r = nullptr;
-    void *vol_l = nullptr, *vol_r = nullptr;   // cost volumes, element type p.vol_dtype
-    float *dsub = nullptr;
-    int16_t *lbl_l = nullptr, *lbl_r = nullptr;
-    float *agg_l = nullptr, *agg_r = nullptr;
-    uint8_t *stage_l = nullptr, *stage_r = nullptr;
-    float *stage_disp = nullptr;
-    int debug = 0;
-    int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
-    bool matched = false, agg_valid = false;
-    bool profiling = false, timed = false;
-    cudaEvent_t ev[kStages + 1] = {};
-    char err[256] = {0};
-};
 
 namespace {
-
-sr_status fail_cuda(sr_ctx *c, cudaError_t e, const char *what) {
-    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
-}
-
-#define SR_TRY(c, expr, what)                           \
-    do {                                                \
-        cudaError_t e_ = (expr);                        \
-        if (e_ != cudaSuccess) return fail_cuda(c, e_, what); \
-    } while (0)
 
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
@@ -129,6 +181,7 @@ void free_all(sr_ctx *c) {
         if (q) cudaFree(q);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    sr_batch_free(c);
 }
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
@@ -148,27 +201,6 @@ float bf16_bits_to_float(uint16_t b) {
     float v;
     memcpy(&v, &u, sizeof(v));
     return v;
-}
-
-// After the stream is synchronised: report (and clear) a device-side timeout.
-sr_status take_device_error(sr_ctx *c) {
-    int h = 0;
-    cudaError_t e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(err)");
-    if (h == 0) return SR_OK;
-    cudaMemset(c->d_err, 0, sizeof(int));
-    snprintf(c->err, sizeof(c->err), "a bounded device wait for a cost-row copy ran out");
-    return SR_ERR_TIMEOUT;
-}
-
-sr::AggDebug agg_debug(const sr_ctx *c) {
-    sr::AggDebug d;
-    d.err = c->d_err;
-    if (c->debug & SR_DEBUG_WITHHOLD_ROW) {
-        d.withhold_last = 1;
-        d.wait_cycles = 2000000;            // ~1 ms
-    }
-    return d;
 }
 
 }  // namespace

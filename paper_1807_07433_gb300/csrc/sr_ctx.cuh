@@ -1,0 +1,72 @@
+// sr_ctx.cuh -- the context behind the opaque sr_ctx of include/sr.h, and the
+// error helpers shared by the ABI translation units.  Not installed.
+#pragma once
+#include <stdio.h>
+
+#include "../../include/sr.h"
+#include "sr_internal.cuh"
+
+constexpr int kStages = 7;    // stages of one sr_match with profiling events
+
+struct SrBatch;               // batched-form state, defined in sr_batch.cu
+void sr_batch_free(sr_ctx *c);
+
+struct sr_ctx {
+    sr_params p{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    double alpha0 = 0, alpha1 = 0, delta = 0;
+    double f_px = 0, baseline = 0, u0 = 0, v0 = 0;
+    bool camera = false;
+    // scratch (owned)
+    float *rw = nullptr, *mu_l = nullptr, *inv_l = nullptr, *mu_r = nullptr, *inv_r = nullptr;
+    void *vol_l = nullptr, *vol_r = nullptr;   // cost volumes, element type p.vol_dtype
+    float *dsub = nullptr;
+    int16_t *lbl_l = nullptr, *lbl_r = nullptr;
+    float *agg_l = nullptr, *agg_r = nullptr;
+    uint8_t *stage_l = nullptr, *stage_r = nullptr;
+    float *stage_disp = nullptr;
+    int debug = 0;
+    int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
+    bool matched = false, agg_valid = false;
+    bool profiling = false, timed = false;
+    cudaEvent_t ev[kStages + 1] = {};
+    char err[256] = {0};
+    SrBatch *batch = nullptr;        // batched-form resources (sr_batch.cu), on first use
+};
+
+namespace {
+
+inline sr_status fail_cuda(sr_ctx *c, cudaError_t e, const char *what) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+}
+
+#define SR_TRY(c, expr, what)                           \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return fail_cuda(c, e_, what); \
+    } while (0)
+
+// After the stream is synchronised: report (and clear) a device-side timeout.
+inline sr_status take_device_error(sr_ctx *c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(err)");
+    if (h == 0) return SR_OK;
+    cudaMemset(c->d_err, 0, sizeof(int));
+    snprintf(c->err, sizeof(c->err), "a bounded device wait for a cost-row copy ran out");
+    return SR_ERR_TIMEOUT;
+}
+
+inline sr::AggDebug agg_debug(const sr_ctx *c) {
+    sr::AggDebug d;
+    d.err = c->d_err;
+    if (c->debug & SR_DEBUG_WITHHOLD_ROW) {
+        d.withhold_last = 1;
+        d.wait_cycles = 2000000;            // ~1 ms
+    }
+    return d;
+}
+
+}  // namespace

@@ -107,4 +107,62 @@ __host__ __device__ inline int clampi(int x, int lo, int hi) {
     return x < lo ? lo : (x > hi ? hi : x);
 }
 
+// One stereo pair of a batch: its inputs, outputs and scratch (device
+// pointers) and plane.  Batched kernels read an array of these and walk a flat
+// list of (pair, tile) work items; tiles of pair p occupy
+// [start[p], start[p+1]) of that list.
+struct PairDesc {
+    int W, H, pitch;
+    const uint8_t *left, *right;
+    double alpha0, alpha1, delta;
+    float *disp;
+    int16_t *wta;                 // nullable
+    float *rw, *mu_l, *inv_l, *mu_r, *inv_r, *dsub;
+    void *vol_l, *vol_r;
+    int16_t *lbl_l, *lbl_r;
+};
+
+// Pair owning flat work item t (start[] ascending, start[0] = 0), searched
+// forward from a previous answer p0 <= the result (a persistent CTA's items
+// only grow, so this is usually zero or one step).
+__device__ __forceinline__ int find_pair(const int *start, int n, int t, int p0 = 0) {
+    int p = p0;
+    while (p + 1 < n && start[p + 1] <= t) ++p;
+    return p;
+}
+
+// Copies start[0..n] into shared memory when it fits (kStartSmem ints), for
+// the persistent kernels' pair search; returns the array to search.
+constexpr int kStartSmem = 256;
+__device__ __forceinline__ const int *stage_start(int *s_start, const int *start, int n) {
+    if (n + 1 > kStartSmem) return start;
+    for (int i = threadIdx.x + threadIdx.y * blockDim.x; i <= n; i += blockDim.x * blockDim.y)
+        s_start[i] = start[i];
+    __syncthreads();
+    return s_start;
+}
+
+// Tiles of each batched stage (tile sizes of the kernels below).
+constexpr int kPixTX = 32, kPixTY = 8;    // per-pixel stages (warp, stats, L-R + post)
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Batched stages: one persistent launch each over all pairs' tiles.
+//   starts: device [n+1] prefix arrays per stage (see sr_batch.cu)
+cudaError_t launch_warp_batch(const PairDesc *pairs, const int *start, int n, int grid,
+                              cudaStream_t st);
+cudaError_t launch_stats_batch(const PairDesc *pairs, const int *start, int n, int D, int ncc_r,
+                               int grid, cudaStream_t st);
+//   next: nullable device counter (zeroed before the launch); when given,
+//   CTAs take work items in order from it instead of striding
+cudaError_t launch_ncc_batch(bool target, const PairDesc *pairs, const int *start, int n, int D,
+                             int ncc_r, int vt, int grid, int *next, cudaStream_t st);
+cudaError_t launch_agg_batch(bool target, const PairDesc *pairs, const int *start, int n, int D,
+                             int agg_r, int vt, float gamma_d, float gamma_r, const AggDebug &dbg,
+                             int grid, int *next, cudaStream_t st);
+cudaError_t launch_lrc_post_batch(const PairDesc *pairs, const int *start, int n, float lr_thresh,
+                                  int grid, cudaStream_t st);
+// Resident CTAs per SM of the batched NCC / aggregation kernels (for grid sizing).
+int ncc_batch_occupancy(int D, int ncc_r, int vt);
+int agg_batch_occupancy(int D, int agg_r, int vt);
+
 }  // namespace sr

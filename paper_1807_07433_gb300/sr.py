@@ -26,7 +26,8 @@ SR_DEBUG_WITHHOLD_ROW = 2
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
-           "sr_match_host", "sr_match_noalloc", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
+           "sr_match_host", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
+           "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
            "sr_set_profiling", "sr_synchronize", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
            "sr_status_str", "sr_last_error", "sr_version")
 
@@ -36,6 +37,14 @@ class sr_params(ctypes.Structure):
                 ("ncc_radius", ctypes.c_int), ("agg_radius", ctypes.c_int),
                 ("gamma_d", ctypes.c_float), ("gamma_r", ctypes.c_float),
                 ("lr_thresh", ctypes.c_float), ("vol_dtype", ctypes.c_int)]
+
+
+class sr_pair_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("pitch_bytes", ctypes.c_int), ("d_left", ctypes.c_void_p),
+                ("d_right", ctypes.c_void_p), ("alpha0", ctypes.c_double),
+                ("alpha1", ctypes.c_double), ("delta", ctypes.c_double),
+                ("d_disp", ctypes.c_void_p), ("d_wta_or_null", ctypes.c_void_p)]
 
 
 class SrError(RuntimeError):
@@ -72,6 +81,10 @@ def load(path: str | None = None):
                 "sr_match_host": (i, [vp, vp, vp, vp]),
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
+                "sr_match_batch": (i, [vp, i, ctypes.POINTER(sr_pair_desc)]),
+                "sr_set_autotune": (i, [vp, i, ctypes.c_char_p]),
+                "sr_batch_info": (i, [vp, ctypes.c_char_p, sz]),
+                "sr_set_batch_schedule": (i, [vp, i]),
                 "sr_reconstruct": (i, [vp, vp, vp]),
                 "sr_get_buffer": (i, [vp, i, vp, ctypes.POINTER(sz)]),
                 "sr_set_debug": (i, [vp, i]),
@@ -168,6 +181,36 @@ def sr_match_noalloc(params: sr_params, alpha0: float, alpha1: float, delta: flo
                                          _ptr(d_left), _ptr(d_right), int(pitch_bytes),
                                          _ptr(d_disp), _ptr(d_wta_or_null),
                                          _stream_handle(cuda_stream)), "sr_match_noalloc")
+
+
+def make_pair_desc(left, right, disp, alpha0, alpha1, delta, wta=None) -> sr_pair_desc:
+    """Descriptor of one pair (torch CUDA tensors [H, W])."""
+    H, W = left.shape
+    return sr_pair_desc(int(W), int(H), int(left.stride(0) * left.element_size()), _ptr(left),
+                        _ptr(right), float(alpha0), float(alpha1), float(delta), _ptr(disp),
+                        _ptr(wta))
+
+
+def sr_match_batch(ctx, pairs) -> None:
+    arr = (sr_pair_desc * len(pairs))(*pairs)
+    _check(ctx, load().sr_match_batch(ctx, len(pairs), arr), "sr_match_batch")
+
+
+def sr_set_autotune(ctx, enable: bool, cache_path: str | None = None) -> None:
+    _check(ctx, load().sr_set_autotune(ctx, int(bool(enable)),
+                                       cache_path.encode() if cache_path else None),
+           "sr_set_autotune")
+
+
+def sr_set_batch_schedule(ctx, variant: int) -> None:
+    _check(ctx, load().sr_set_batch_schedule(ctx, int(variant)), "sr_set_batch_schedule")
+
+
+def sr_batch_info(ctx) -> dict:
+    import json
+    buf = ctypes.create_string_buffer(1024)
+    _check(ctx, load().sr_batch_info(ctx, buf, 1024), "sr_batch_info")
+    return json.loads(buf.value.decode())
 
 
 def sr_reconstruct(ctx, d_disp, d_xyz) -> None:

@@ -15,7 +15,8 @@ Recipe (all randomness from numpy PCG64 seeded per scene):
     lattice points (defined at any real x), rescaled to mean 128, std 40
     over the left image;
   * disparity d(u,v) = alpha0 + alpha1*v - min(2, potholes + grooves); a
-    pothole is A*exp(-r^2/(2 s^2)), A ~ U[0.5,2], s ~ U[5,12] px; a groove is
+    pothole is A*exp(-r^2/(2 s^2)) within 4 s of its centre, A ~ U[0.5,2],
+    s ~ U[5,12] px; a groove is
     a random 3-segment polyline with a triangular profile 1-3 px wide and
     0.5-2 px deep;
   * left(u,v) = T(u,v); right(u_r,v) = T(u_l,v) with u_l = u_r + d(u_l,v)
@@ -116,16 +117,33 @@ def _depressions(rng: np.random.Generator, sc: Scene):
 
 
 def _depth(u: np.ndarray, v: np.ndarray, pots, grooves) -> np.ndarray:
-    dep = np.zeros(np.broadcast(u, v).shape, np.float64)
+    """Total depression at points (u[r, c], row r); v[r, :] == r.  Each feature
+    is evaluated on the rows it reaches (a pothole within 4 sigma, a groove
+    within its segment's rows plus its half width)."""
+    H = u.shape[0]
+    dep = np.zeros(u.shape, np.float64)
     for (uk, vk, a, s) in pots:
-        dep += a * np.exp(-((u - uk) ** 2 + (v - vk) ** 2) / (2.0 * s * s))
+        r0, r1 = max(0, int(vk - 4 * s)), min(H, int(vk + 4 * s) + 2)
+        if r0 >= r1:
+            continue
+        uu, vv = u[r0:r1], v[r0:r1]
+        dep[r0:r1] += a * np.exp(-((uu - uk) ** 2 + (vv - vk) ** 2) / (2.0 * s * s))
     for pts, half_w, depth in grooves:
         dist = np.full(dep.shape, np.inf)
+        rows = np.zeros(H, bool)
         for (x0, y0), (x1, y1) in zip(pts[:-1], pts[1:]):
+            r0 = max(0, int(min(y0, y1) - half_w) - 1)
+            r1 = min(H, int(max(y0, y1) + half_w) + 2)
+            if r0 >= r1:
+                continue
+            rows[r0:r1] = True
+            uu, vv = u[r0:r1], v[r0:r1]
             ex, ey = x1 - x0, y1 - y0
-            t = np.clip(((u - x0) * ex + (v - y0) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
-            dist = np.minimum(dist, np.hypot(u - (x0 + t * ex), v - (y0 + t * ey)))
-        dep += depth * np.clip(1.0 - dist / half_w, 0.0, None)
+            t = np.clip(((uu - x0) * ex + (vv - y0) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
+            dist[r0:r1] = np.minimum(dist[r0:r1],
+                                     np.hypot(uu - (x0 + t * ex), vv - (y0 + t * ey)))
+        if rows.any():
+            dep[rows] += depth * np.clip(1.0 - dist[rows] / half_w, 0.0, None)
     return np.minimum(dep, 2.0)
 
 

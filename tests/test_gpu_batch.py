@@ -1,0 +1,143 @@
+"""Batched form: sr_match_batch over pairs of mixed sizes equals sr_match on
+each pair (same tile kernels, so the results are bit-identical), across graph
+replays, schedules chosen by the autotuner, and FP16 volumes."""
+import numpy as np
+import pytest
+
+from paper_1807_07433_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(97, 45), (160, 120), (203, 77), (64, 33), (160, 120), (31, 9)]
+D, NCC_R, AGG_R, GD, GR = 32, 2, 3, 3.0, 10.0
+
+
+def _pairs(seed0):
+    out = []
+    for k, (W, H) in enumerate(SIZES):
+        sc = synth.Scene(W, H, 8.0 + k, 0.03 + 0.01 * k, 2, False, seed0 + k)
+        left, right, _ = synth.make_pair(sc)
+        out.append((left, right, sc.alpha0, sc.alpha1, 6.0 + (k % 3)))
+    return out
+
+
+def _single(pairs, vt):
+    import torch
+    from paper_1807_07433_gb300 import sr
+    res = []
+    for left, right, a0, a1, dl in pairs:
+        H, W = left.shape
+        with sr.Matcher(W, H, D, NCC_R, AGG_R, GD, GR, vol_dtype=vt,
+                        stream=torch.cuda.current_stream()) as m:
+            m.set_plane(a0, a1, dl)
+            wta = torch.empty((H, W), dtype=torch.int16, device="cuda")
+            disp = m.match(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(), wta=wta)
+            torch.cuda.synchronize()
+            res.append((disp.cpu().numpy(), wta.cpu().numpy()))
+    return res
+
+
+def _batch(ctx, pairs, order=None):
+    import torch
+    from paper_1807_07433_gb300 import sr
+    order = list(range(len(pairs))) if order is None else order
+    keep, descs, outs = [], [], {}
+    for i in order:
+        left, right, a0, a1, dl = pairs[i]
+        H, W = left.shape
+        tl, tr = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+        disp = torch.full((H, W), -3.0, device="cuda")
+        wta = torch.full((H, W), -3, dtype=torch.int16, device="cuda")
+        keep += [tl, tr]
+        outs[i] = (disp, wta)
+        descs.append(sr.make_pair_desc(tl, tr, disp, a0, a1, dl, wta))
+    sr.sr_match_batch(ctx, descs)
+    sr.sr_synchronize(ctx)
+    return {i: (d.cpu().numpy(), w.cpu().numpy()) for i, (d, w) in outs.items()}
+
+
+def _same(got, want):
+    for i, (d, w) in want.items() if isinstance(want, dict) else enumerate(want):
+        gd, gw = got[i]
+        np.testing.assert_array_equal(gw, w)
+        np.testing.assert_array_equal(np.isnan(gd), np.isnan(d))
+        fin = np.isfinite(d)
+        np.testing.assert_array_equal(gd[fin], d[fin])
+
+
+def _ctx(vt=0):
+    import torch
+    from paper_1807_07433_gb300 import sr
+    return sr.Matcher(8, 8, D, NCC_R, AGG_R, GD, GR, vol_dtype=vt,
+                      stream=torch.cuda.current_stream())
+
+
+@pytest.mark.parametrize("vt", [0, 1])
+def test_batch_equals_single_calls_and_replays(vt):
+    from paper_1807_07433_gb300 import sr
+    p1, p2 = _pairs(100), _pairs(200)
+    with _ctx(vt) as m:
+        _same(_batch(m.ctx, p1), _single(p1, vt))
+        # graph replay with new images, planes and a new pair order
+        _same(_batch(m.ctx, p2, order=[5, 3, 1, 0, 2, 4]), _single(p2, vt))
+        info = sr.sr_batch_info(m.ctx)
+        assert info["pairs"] == len(SIZES) and info["schedule"] == "persistent"
+
+
+@pytest.mark.parametrize("variant", [1, 2, 4, 5])
+def test_every_schedule_equals_single_calls(variant):
+    from paper_1807_07433_gb300 import sr
+    p1, p2 = _pairs(500), _pairs(600)
+    with _ctx() as m:
+        sr.sr_set_batch_schedule(m.ctx, variant)
+        _same(_batch(m.ctx, p1), _single(p1, 0))
+        _same(_batch(m.ctx, p2, order=[2, 0, 1, 5, 4, 3]), _single(p2, 0))
+        info = sr.sr_batch_info(m.ctx)
+        assert info["variant"] == variant
+        assert info["schedule"] == ("per-pair-streams" if variant >= 4 else "persistent")
+        with pytest.raises(sr.SrError):
+            sr.sr_set_batch_schedule(m.ctx, 6)
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    from paper_1807_07433_gb300 import sr
+    cache = str(tmp_path / "tune.jsonl")
+    p = _pairs(300)
+    want = _single(p, 0)
+    with _ctx() as m:
+        sr.sr_set_autotune(m.ctx, True, cache)
+        _same(_batch(m.ctx, p), want)
+        info = sr.sr_batch_info(m.ctx)
+        assert min(info["tune_ms"]) > 0.0          # every candidate was timed
+        assert len(info["tune_ms"]) == 6
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and '"variant": %d' % info["variant"] in lines[0]
+    with _ctx() as m:                               # a new context reuses the choice
+        sr.sr_set_autotune(m.ctx, True, cache)
+        _same(_batch(m.ctx, p), want)
+        info2 = sr.sr_batch_info(m.ctx)
+        assert info2["variant"] == info["variant"] and max(info2["tune_ms"]) == 0.0
+
+
+def test_corrupted_tune_cache_falls_back_and_reports(tmp_path):
+    from paper_1807_07433_gb300 import sr
+    cache = tmp_path / "tune.jsonl"
+    cache.write_text('{"key": "x", "variant": 99}\nnot json at all\n')
+    p = _pairs(400)
+    with _ctx() as m:
+        sr.sr_set_autotune(m.ctx, True, str(cache))
+        assert b"unreadable" in sr.load().sr_last_error(m.ctx)
+        _same(_batch(m.ctx, p), _single(p, 0))
+
+
+def test_batch_rejects_bad_pairs():
+    import torch
+    from paper_1807_07433_gb300 import sr
+    t = torch.zeros((8, 8), dtype=torch.uint8, device="cuda")
+    d = torch.empty((8, 8), device="cuda")
+    with _ctx() as m:
+        bad = sr.make_pair_desc(t, t, d, 1.0, 0.0, 0.0)
+        bad.pitch_bytes = 4
+        with pytest.raises(sr.SrError) as e:
+            sr.sr_match_batch(m.ctx, [bad])
+        assert e.value.status == sr.SR_ERR_INVALID_ARG
