@@ -89,6 +89,8 @@ def _load():
                 "orc_match": (i, [pp, vp, vp, i, i, ctypes.POINTER(_Outputs)]),
                 "orc_match_pixels": (i, [pp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp,
                                          vp, vp, vp]),
+                "orc_objective": (d, [pp, vp, vp, vp]),
+                "orc_grad": (i, [pp, vp, vp, vp, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -292,3 +294,26 @@ def match_pixels(p: Params, left: np.ndarray, right: np.ndarray, us, vs) -> dict
     if rc != 0:
         raise RuntimeError(f"orc_match_pixels failed with {rc}")
     return out
+
+
+def objective(p: Params, left, right, dstar) -> float:
+    """L = sum of the aggregated reference cost at fixed disparities dstar
+    (int, -1 = pixel left out); left/right real-valued images."""
+    L, R = _f64(left), _f64(right)
+    ds = np.ascontiguousarray(dstar, dtype=np.int32)
+    return _load().orc_objective(ctypes.byref(p.c()), _ptr(L), _ptr(R), _ptr(ds))
+
+
+def grad(p: Params, left, right, dstar):
+    """(L, dL/dalpha [2], dL/dleft [H,W], dL/dright [H,W]) in FP64."""
+    L, R = _f64(left), _f64(right)
+    ds = np.ascontiguousarray(dstar, dtype=np.int32)
+    out_l = ctypes.c_double()
+    da = np.zeros(2)
+    gl = np.zeros((p.H, p.W))
+    gr = np.zeros((p.H, p.W))
+    rc = _load().orc_grad(ctypes.byref(p.c()), _ptr(L), _ptr(R), _ptr(ds), ctypes.byref(out_l),
+                          _ptr(da), _ptr(gl), _ptr(gr))
+    if rc != 0:
+        raise RuntimeError(f"orc_grad failed with {rc}")
+    return out_l.value, da, gl, gr

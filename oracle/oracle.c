@@ -478,3 +478,169 @@ int orc_match_pixels(const orc_params *p, const uint8_t *il, const uint8_t *ir, 
     free(L); free(R);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Objective and gradient for refining the road plane (Sec. II-A, Eq. 2).
+ *
+ * L(alpha) = sum over pixels p with dstar[p] >= 0 of the aggregated reference
+ * cost c_agg(p, dstar[p]) (Eq. 8), the disparities dstar held fixed.  Images
+ * are real-valued here (double), so that derivatives with respect to pixel
+ * values exist; ir is the original target image, warped inside.
+ * ------------------------------------------------------------------------ */
+
+/* Sec. II-A warp of a real-valued target image; also d(warped)/ds per pixel. */
+static void warp_real(const orc_params *p, const double *ir, double *out, double *dds) {
+    const int W = p->W, H = p->H;
+    for (int v = 0; v < H; ++v) {
+        const double s = orc_row_shift(p, v);
+        const double k = floor(s);
+        const double w = s - k;
+        const int ki = (int)k;
+        for (int x = 0; x < W; ++x) {
+            const double a = ir[(size_t)v * W + clampi(x - ki, 0, W - 1)];
+            const double b = ir[(size_t)v * W + clampi(x - ki - 1, 0, W - 1)];
+            out[(size_t)v * W + x] = (1.0 - w) * a + w * b;
+            if (dds) dds[(size_t)v * W + x] = b - a;   /* d/ds of (1-w) a + w b, w = s - k */
+        }
+    }
+}
+
+double orc_objective(const orc_params *p, const double *il, const double *ir, const int32_t *dstar) {
+    const int W = p->W, H = p->H, rho = p->agg_r;
+    double *R = (double *)malloc((size_t)W * H * sizeof(double));
+    if (!R) return NAN;
+    warp_real(p, ir, R, NULL);
+    double L = 0.0;
+    #pragma omp parallel for reduction(+ : L) schedule(dynamic, 1)
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            const int d = dstar[(size_t)v * W + u];
+            if (d < 0) continue;
+            const double gc = il[(size_t)v * W + u];
+            double num = 0.0, den = 0.0;
+            for (int dy = -rho; dy <= rho; ++dy) {
+                const int y = v + dy;
+                if (y < 0 || y >= H) continue;
+                for (int dx = -rho; dx <= rho; ++dx) {
+                    const int x = u + dx;
+                    if (x < 0 || x >= W) continue;
+                    const double wd = exp(-(double)(dx * dx + dy * dy) / (p->gamma_d * p->gamma_d));
+                    const double di = il[(size_t)y * W + x] - gc;
+                    const double wr = exp(-(di * di) / (p->gamma_r * p->gamma_r));
+                    num += wd * wr * orc_ncc(il, R, W, H, p->ncc_r, x, x - d, y);
+                    den += wd * wr;
+                }
+            }
+            L += num / den;
+        }
+    }
+    free(R);
+    return L;
+}
+
+/* Analytic gradient of orc_objective by the chain rule, in FP64:
+ *   c_agg = sum_k w_k c_k / sum_k w_k, w_k = omega_d omega_r(i_l(n_k) - i_l(p))
+ *     d c_agg / d c_k = w_k / W;  d c_agg / d w_k = (c_k - c_agg) / W;
+ *     d omega_r / d delta = -2 delta / gamma_r^2 * omega_r            (Eq. 10)
+ *   c = sum a b / (n sig_l sig_r), a, b the centred blocks            (Eq. 3)
+ *     d c / d r_j = (a_j - c (sig_l / sig_r) b_j) / (n sig_l sig_r)
+ *     d c / d l_j = (b_j - c (sig_r / sig_l) a_j) / (n sig_l sig_r)
+ *   r = i_r'(x, v) = (1-w) i_r(x-k) + w i_r(x-k-1), s = alpha0 + alpha1 v - delta
+ *     d r / d s = i_r(x-k-1) - i_r(x-k);  d s / d alpha = (1, v)
+ * Writes L, dL/dalpha (2 values) and, when not NULL, dL/d i_l and dL/d i_r
+ * (H*W each).  Returns 0, or -2 on allocation failure. */
+int orc_grad(const orc_params *p, const double *il, const double *ir, const int32_t *dstar,
+             double *L_out, double *dalpha, double *gl, double *gr) {
+    const int W = p->W, H = p->H, rho = p->agg_r, r = p->ncc_r;
+    const size_t npx = (size_t)W * H;
+    const double n = (double)((2 * r + 1) * (2 * r + 1));
+    double *R = (double *)malloc(npx * sizeof(double));
+    double *dds = (double *)malloc(npx * sizeof(double));
+    double *gR = (double *)calloc(npx, sizeof(double));     /* dL / d i_r' */
+    double *gL = (double *)calloc(npx, sizeof(double));     /* dL / d i_l  */
+    if (!R || !dds || !gR || !gL) { free(R); free(dds); free(gR); free(gL); return -2; }
+    warp_real(p, ir, R, dds);
+    double L = 0.0;
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            const int d = dstar[(size_t)v * W + u];
+            if (d < 0) continue;
+            const double gc = il[(size_t)v * W + u];
+            /* weights and costs of the window */
+            double wk[256], ck[256], dk[256];
+            int xk[256], yk[256], m = 0;
+            double Wsum = 0.0, num = 0.0;
+            for (int dy = -rho; dy <= rho; ++dy) {
+                const int y = v + dy;
+                if (y < 0 || y >= H) continue;
+                for (int dx = -rho; dx <= rho; ++dx) {
+                    const int x = u + dx;
+                    if (x < 0 || x >= W) continue;
+                    const double wd = exp(-(double)(dx * dx + dy * dy) / (p->gamma_d * p->gamma_d));
+                    const double di = il[(size_t)y * W + x] - gc;
+                    const double wr = exp(-(di * di) / (p->gamma_r * p->gamma_r));
+                    wk[m] = wd * wr;
+                    dk[m] = di;
+                    ck[m] = orc_ncc(il, R, W, H, r, x, x - d, y);
+                    xk[m] = x;
+                    yk[m] = y;
+                    Wsum += wk[m];
+                    num += wk[m] * ck[m];
+                    ++m;
+                }
+            }
+            const double cagg = num / Wsum;
+            L += cagg;
+            for (int k = 0; k < m; ++k) {
+                /* through the weight w_k (guide = left image) */
+                const double gw = (ck[k] - cagg) / Wsum * wk[k] *
+                                  (-2.0 * dk[k] / (p->gamma_r * p->gamma_r));
+                gL[(size_t)yk[k] * W + xk[k]] += gw;
+                gL[(size_t)v * W + u] -= gw;
+                /* through the cost c_k = NCC(left block n_k, right block n_k - d) */
+                const double beta = wk[k] / Wsum;
+                double mu_l, sg_l, mu_r, sg_r;
+                const double var_l = orc_block_stats(il, W, H, r, xk[k], yk[k], &mu_l, &sg_l);
+                const double var_r = orc_block_stats(R, W, H, r, xk[k] - d, yk[k], &mu_r, &sg_r);
+                if (var_l < ORC_FLAT_VAR || var_r < ORC_FLAT_VAR) continue;   /* c == 0 */
+                const double c = ck[k], den = n * sg_l * sg_r;
+                for (int j = -r; j <= r; ++j) {
+                    const int y = clampi(yk[k] + j, 0, H - 1);
+                    for (int i = -r; i <= r; ++i) {
+                        const size_t li = (size_t)y * W + clampi(xk[k] + i, 0, W - 1);
+                        const size_t ri = (size_t)y * W + clampi(xk[k] - d + i, 0, W - 1);
+                        const double a = il[li] - mu_l, b = R[ri] - mu_r;
+                        gR[ri] += beta * (a - c * (sg_l / sg_r) * b) / den;
+                        gL[li] += beta * (b - c * (sg_r / sg_l) * a) / den;
+                    }
+                }
+            }
+        }
+    }
+    double g0 = 0.0, g1 = 0.0;
+    for (int v = 0; v < H; ++v)
+        for (int x = 0; x < W; ++x) {
+            const double t = gR[(size_t)v * W + x] * dds[(size_t)v * W + x];
+            g0 += t;
+            g1 += t * (double)v;
+        }
+    if (L_out) *L_out = L;
+    if (dalpha) { dalpha[0] = g0; dalpha[1] = g1; }
+    if (gl) memcpy(gl, gL, npx * sizeof(double));
+    if (gr) {
+        /* adjoint of the warp: i_r'(x) = (1-w) i_r(x-k) + w i_r(x-k-1) */
+        memset(gr, 0, npx * sizeof(double));
+        for (int v = 0; v < H; ++v) {
+            const double s = orc_row_shift(p, v);
+            const double k = floor(s), w = s - k;
+            const int ki = (int)k;
+            for (int x = 0; x < W; ++x) {
+                const double g = gR[(size_t)v * W + x];
+                gr[(size_t)v * W + clampi(x - ki, 0, W - 1)] += (1.0 - w) * g;
+                gr[(size_t)v * W + clampi(x - ki - 1, 0, W - 1)] += w * g;
+            }
+        }
+    }
+    free(R); free(dds); free(gR); free(gL);
+    return 0;
+}
