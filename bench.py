@@ -482,6 +482,81 @@ def batch_report(steps: int, warmup: int):
             "l2": "flushed between timed steps", "forms": res}
 
 
+def adjoint_report(steps: int, warmup: int):
+    """Plane refinement on the 1280x720 D64 NCC 7x7 bilateral 11x11 workload:
+    time of one sr_grad_plane (L and dL/dalpha, plane hypothesis: every pixel
+    at residual delta), then refinement (L-BFGS and Adam, at most 50
+    evaluations each) from the true plane perturbed by (U[-1.5, 1.5] px,
+    U[-0.01, 0.01] px/row), seed 5, on the scene with potholes and grooves and
+    on the same road without them.  Errors are in pixels: alpha0 and the
+    alpha1 shift accumulated over the frame, alpha1 (H-1)."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_1807_07433_gb300 import refine, sr, synth
+    w = synth.C2
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    out = {"report": "adjoint", "workload": w.name, "objective": "sum_p c_agg(p, delta)",
+           "steps": steps, "warmup": warmup}
+    scenes = {"with_depressions": w.scene,
+              "plain_road": dataclasses.replace(w.scene, n_potholes=0, grooves=False)}
+    for key, sc in scenes.items():
+        left, right, _ = synth.make_pair(sc)
+        H, W = left.shape
+        with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, stream=stream) as m:
+            dl, dr = torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)
+            dstar = torch.full((H, W), int(w.delta), dtype=torch.int16, device=dev)
+            ev = refine.MatcherEvaluator(m, dl, dr, dstar, w.delta)
+            ent = {}
+            if key == "with_depressions":
+                for _ in range(warmup):
+                    ev.value_and_grad(sc.alpha0 + 0.3, sc.alpha1)
+                ms = []
+                for _ in range(steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.set_plane(sc.alpha0 + 0.3, sc.alpha1, w.delta)
+                    sr.sr_grad_plane(m.ctx, dl, dr, W, dstar)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                ent["grad_ms_median"] = round(statistics.median(ms), 3)
+                gl = torch.empty((H, W), dtype=torch.float32, device=dev)
+                gr = torch.empty_like(gl)
+                ms = []
+                for _ in range(max(3, steps // 4)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sr.sr_grad_plane(m.ctx, dl, dr, W, dstar, gl, gr)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                ent["grad_with_image_grads_ms_median"] = round(statistics.median(ms), 3)
+            rng = np.random.default_rng(5)
+            a_init = (sc.alpha0 + rng.uniform(-1.5, 1.5), sc.alpha1 + rng.uniform(-0.01, 0.01))
+            L_true = ev.value_and_grad(sc.alpha0, sc.alpha1)[0]
+            ent.update({"alpha_true": [sc.alpha0, sc.alpha1], "alpha_init": list(a_init),
+                        "err_init_px": [a_init[0] - sc.alpha0,
+                                        (a_init[1] - sc.alpha1) * (H - 1)],
+                        "L_true_plane": L_true})
+            for method in ("lbfgs", "adam"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = refine.refine_plane(ev, a_init, H, max_evals=50, method=method)
+                t_ref = time.perf_counter() - t0
+                ent[method] = {
+                    "evaluations": len(res.history), "alpha_final": list(res.alpha),
+                    "err_final_px": [res.alpha[0] - sc.alpha0,
+                                     (res.alpha[1] - sc.alpha1) * (H - 1)],
+                    "L_init": res.history[0][2], "L_final": max(h[2] for h in res.history),
+                    "wall_s": round(t_ref, 3)}
+            out[key] = ent
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,7 +564,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--report", choices=("precision", "batch"), default=None,
+    ap.add_argument("--report", choices=("precision", "batch", "adjoint"), default=None,
                     help="print a report instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -499,6 +574,9 @@ def main():
         return
     if args.report == "batch":
         print(json.dumps(batch_report(args.steps, args.warmup)), flush=True)
+        return
+    if args.report == "adjoint":
+        print(json.dumps(adjoint_report(args.steps, args.warmup)), flush=True)
         return
     from paper_1807_07433_gb300 import synth
     w = synth.C2

@@ -205,6 +205,37 @@ sr_status sr_batch_info(sr_ctx *ctx, char *buf, size_t size);
  * NaN or not positive.  Asynchronous.  SR_ERR_STATE if no camera is set. */
 sr_status sr_reconstruct(sr_ctx *ctx, const float *d_disp, float *d_xyz);
 
+/* Gradient of the aggregated matching cost with respect to the road plane,
+ * for refining alpha (Sec. II-A, Eq. 2) by gradient ascent.  The paper fits
+ * alpha once from a disparity map (Sec. II-A) and has no gradient; this is
+ * the adjoint of its own cost, by the chain rule through the warp (Sec.
+ * II-A), the NCC (Eqs. 3-5) and the bilateral aggregation of the reference
+ * volume (Eqs. 8-10, guide = left image):
+ *   L(alpha) = sum over pixels p with d_dstar[p] >= 0 of c_agg(p, d_dstar[p]),
+ * with the disparities d_dstar held fixed (the plane hypothesis is every
+ * pixel at residual delta; the winning labels of sr_match are another set).
+ * The warp and block statistics are recomputed at the context's current
+ * plane (sr_set_plane), so the call does not depend on an earlier sr_match.
+ *   d_left, d_right   8-bit images, pitch_bytes >= W, as for sr_match
+ *   d_dstar           int16 [H][W] dense residual disparities; a value
+ *                     outside 0..D-1 (e.g. -1) leaves the pixel out of L
+ *   h_out3            host double[3]: L, dL/dalpha0, dL/dalpha1
+ *   d_grad_left, d_grad_right
+ *                     float [H][W] dense or NULL: dL/di_l and dL/di_r, the
+ *                     images read as real values (FP32 atomics: the last
+ *                     bits vary from run to run; L and dL/dalpha are summed
+ *                     in FP64 in a fixed order and do not)
+ * Arithmetic is FP32 per term with FP64 sums.  The objective is piecewise
+ * smooth in alpha: it has kinks where a row shift alpha0 + alpha1 v - delta
+ * crosses an integer.  Synchronises the context's stream (h_out3 is host
+ * memory).  The context's cost volumes serve as scratch (the buffers of
+ * the last sr_match are no longer available to sr_get_buffer afterwards);
+ * the first call allocates about 12*W*H bytes more, plus 8*W*H*D bytes
+ * for FP32 copies when the context stores 16-bit volumes. */
+sr_status sr_grad_plane(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                        int pitch_bytes, const int16_t *d_dstar, double *h_out3,
+                        float *d_grad_left, float *d_grad_right);
+
 /* Intermediate arrays of the last sr_match, for inspection and tests.
  * which selects the array; its device layout and element type are fixed:
  *   SR_BUF_WARPED     float [H][W]        warped target i_r' (Sec. II-A)

@@ -176,7 +176,7 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(sr_ctx *c) {
     void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
                     c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
-                    c->stage_disp, c->d_err};
+                    c->stage_disp, c->d_err, c->g_vol, c->g_wsum, c->g_rw, c->g_partial};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)
@@ -415,6 +415,53 @@ sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {
                              d_xyz, c->st),
            "xyz");
     return SR_OK;
+}
+
+sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
+                        const int16_t *d_dstar, double *h_out3, float *d_grad_left,
+                        float *d_grad_right) {
+    if (!c || !d_left || !d_right || !d_dstar || !h_out3 || pitch_bytes < c->p.width)
+        return SR_ERR_INVALID_ARG;
+    const sr_params &p = c->p;
+    const int W = p.width, H = p.height, D = p.max_disp;
+    const size_t npx = (size_t)W * H;
+    const size_t nparts = sr::grad_partial_count(W, H) * 3;
+    if (!c->g_wsum) {
+        SR_TRY(c, dalloc(&c->g_wsum, npx), "cudaMalloc(grad wsum)");
+        SR_TRY(c, dalloc(&c->g_rw, npx), "cudaMalloc(grad rw)");
+        SR_TRY(c, dalloc(&c->g_partial, nparts + 3), "cudaMalloc(grad partial)");
+    }
+    // FP32 reference volume and G volume: the context's own cost volumes when
+    // they are FP32, else two FP32 volumes of its own (allocated once)
+    float *cost = (float *)c->vol_l, *G = (float *)c->vol_r;
+    if (p.vol_dtype != SR_VOL_F32) {
+        if (!c->g_vol) {
+            SR_TRY(c, dalloc(&c->g_vol, 2 * npx * D), "cudaMalloc(grad volumes)");
+        }
+        cost = c->g_vol;
+        G = c->g_vol + npx * D;
+    }
+    cudaStream_t st = c->st;
+    c->matched = false;   // the context's scratch no longer holds the last sr_match
+    SR_TRY(c, sr::launch_warp(d_right, pitch_bytes, W, H, c->alpha0, c->alpha1, c->delta, c->rw, st),
+           "warp");
+    SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
+                               c->mu_r, c->inv_r, st),
+           "stats");
+    SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                             c->inv_r, W, H, D, p.ncc_radius, cost, sr::kVolF32, st),
+           "ncc_ref");
+    double *out3 = c->g_partial + nparts;
+    SR_TRY(c, sr::launch_grad(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, p.agg_radius,
+                              p.gamma_d, p.gamma_r, c->alpha0, c->alpha1, c->delta, c->rw, c->mu_l,
+                              c->inv_l, c->mu_r, c->inv_r, cost, d_dstar, c->g_wsum, G,
+                              d_grad_right ? c->g_rw : nullptr, d_grad_left, d_grad_right,
+                              c->g_partial, out3, st),
+           "grad");
+    SR_TRY(c, cudaMemcpyAsync(h_out3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st),
+           "D2H grad");
+    SR_TRY(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return take_device_error(c);
 }
 
 sr_status sr_get_buffer(sr_ctx *c, sr_buffer which, void *dst, size_t *bytes_inout) {

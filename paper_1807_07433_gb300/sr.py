@@ -27,7 +27,8 @@ SR_DEBUG_WITHHOLD_ROW = 2
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
            "sr_match_host", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
-           "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_get_buffer", "sr_set_debug",
+           "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
+           "sr_get_buffer", "sr_set_debug",
            "sr_set_profiling", "sr_synchronize", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
            "sr_status_str", "sr_last_error", "sr_version")
 
@@ -86,6 +87,7 @@ def load(path: str | None = None):
                 "sr_batch_info": (i, [vp, ctypes.c_char_p, sz]),
                 "sr_set_batch_schedule": (i, [vp, i]),
                 "sr_reconstruct": (i, [vp, vp, vp]),
+                "sr_grad_plane": (i, [vp, vp, vp, i, vp, ctypes.POINTER(d), vp, vp]),
                 "sr_get_buffer": (i, [vp, i, vp, ctypes.POINTER(sz)]),
                 "sr_set_debug": (i, [vp, i]),
                 "sr_set_profiling": (i, [vp, i]),
@@ -217,6 +219,16 @@ def sr_reconstruct(ctx, d_disp, d_xyz) -> None:
     _check(ctx, load().sr_reconstruct(ctx, _ptr(d_disp), _ptr(d_xyz)), "sr_reconstruct")
 
 
+def sr_grad_plane(ctx, d_left, d_right, pitch_bytes: int, d_dstar, d_grad_left=None,
+                  d_grad_right=None) -> np.ndarray:
+    """Returns [L, dL/dalpha0, dL/dalpha1]; fills the optional image gradients."""
+    out = (ctypes.c_double * 3)()
+    _check(ctx, load().sr_grad_plane(ctx, _ptr(d_left), _ptr(d_right), int(pitch_bytes),
+                                     _ptr(d_dstar), out, _ptr(d_grad_left), _ptr(d_grad_right)),
+           "sr_grad_plane")
+    return np.array(out[:], np.float64)
+
+
 def sr_get_buffer(ctx, which: int, dst, nbytes: int) -> int:
     n = ctypes.c_size_t(nbytes)
     _check(ctx, load().sr_get_buffer(ctx, int(which), _ptr(dst), ctypes.byref(n)),
@@ -324,6 +336,24 @@ class Matcher:
             xyz = torch.empty((3, self.H, self.W), dtype=torch.float32, device=disp.device)
         sr_reconstruct(self.ctx, disp, xyz)
         return xyz
+
+    def grad_plane(self, left, right, dstar, image_grads=False):
+        """L and dL/dalpha of the aggregated cost at fixed disparities dstar
+        (int16 [H, W] CUDA tensor, -1 = left out), at the current plane.
+        Returns (L, dL/dalpha [2]) or, with image_grads, also dL/di_l and
+        dL/di_r as float32 [H, W] CUDA tensors."""
+        import torch
+        assert dstar.dtype == torch.int16 and dstar.is_contiguous()
+        pitch = left.stride(0) * left.element_size()
+        assert right.stride(0) == left.stride(0), "left and right must share a pitch"
+        gl = gr = None
+        if image_grads:
+            gl = torch.empty((self.H, self.W), dtype=torch.float32, device=left.device)
+            gr = torch.empty_like(gl)
+        out = sr_grad_plane(self.ctx, left, right, pitch, dstar, gl, gr)
+        if image_grads:
+            return float(out[0]), out[1:].copy(), gl, gr
+        return float(out[0]), out[1:].copy()
 
     def buffer(self, which: int) -> np.ndarray:
         dt, vol = _BUF_SPEC[which]

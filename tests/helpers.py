@@ -81,3 +81,17 @@ def label_report(gpu_lbl, orc_lbl, orc_gap):
     diff = gpu_lbl.astype(np.int64) != orc_lbl.astype(np.int64)
     bad = diff & ~(orc_gap < TAU_TIE)
     return 1.0 - diff.mean(), int(bad.sum())
+
+
+def kink_free_alpha(a0, a1, delta, H, h0, h1, step=0.0071):
+    """alpha0 near a0 such that every row shift s(v) = alpha0 + alpha1 v - delta
+    (Sec. II-A) stays more than ten steps from an integer, where the linear
+    warp has a kink; a step h1 in alpha1 moves row v by h1 * v."""
+    v = np.arange(H)
+    for _ in range(400):
+        s = a0 + a1 * v - delta
+        frac = s - np.floor(s)
+        if np.minimum(frac, 1.0 - frac).min() > 10.0 * max(h0, h1 * (H - 1)):
+            return a0
+        a0 += step
+    raise AssertionError("no kink-free alpha0 found")

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from helpers import kink_free_alpha
 from paper_1807_07433_gb300 import synth
 
 H_A0 = 1e-3
@@ -31,16 +32,8 @@ def _params(w, a0, a1):
 
 def _kink_free_alpha(w, h0, h1):
     """alpha near the true plane with every row shift >= 10 steps from an integer."""
-    v = np.arange(w.scene.H)
-    a0, a1 = w.scene.alpha0 + 0.137, w.scene.alpha1 + 0.0013
-    for _ in range(200):
-        s = a0 + a1 * v - w.delta
-        frac = s - np.floor(s)
-        margin = np.minimum(frac, 1.0 - frac)
-        if margin.min() > 10.0 * max(h0, h1 * v.max()):
-            return a0, a1
-        a0 += 0.0071
-    raise AssertionError("no kink-free alpha found")
+    a1 = w.scene.alpha1 + 0.0013
+    return kink_free_alpha(w.scene.alpha0 + 0.137, a1, w.delta, w.scene.H, h0, h1), a1
 
 
 @pytest.mark.parametrize("objective", ["plane", "winning"])
