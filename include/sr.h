@@ -228,10 +228,10 @@ sr_status sr_reconstruct(sr_ctx *ctx, const float *d_disp, float *d_xyz);
  * Arithmetic is FP32 per term with FP64 sums.  The objective is piecewise
  * smooth in alpha: it has kinks where a row shift alpha0 + alpha1 v - delta
  * crosses an integer.  Synchronises the context's stream (h_out3 is host
- * memory).  The context's cost volumes serve as scratch (the buffers of
- * the last sr_match are no longer available to sr_get_buffer afterwards);
- * the first call allocates about 12*W*H bytes more, plus 8*W*H*D bytes
- * for FP32 copies when the context stores 16-bit volumes. */
+ * memory).  The context's scratch is reused (the buffers of the last
+ * sr_match are no longer available to sr_get_buffer afterwards); the first
+ * call allocates about 12*W*H bytes more, plus 4*W*H*D bytes for an FP32
+ * cost volume when the context stores 16-bit volumes. */
 sr_status sr_grad_plane(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                         int pitch_bytes, const int16_t *d_dstar, double *h_out3,
                         float *d_grad_left, float *d_grad_right);

@@ -431,15 +431,12 @@ sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right
         SR_TRY(c, dalloc(&c->g_rw, npx), "cudaMalloc(grad rw)");
         SR_TRY(c, dalloc(&c->g_partial, nparts + 3), "cudaMalloc(grad partial)");
     }
-    // FP32 reference volume and G volume: the context's own cost volumes when
-    // they are FP32, else two FP32 volumes of its own (allocated once)
-    float *cost = (float *)c->vol_l, *G = (float *)c->vol_r;
+    // FP32 reference volume: the context's own when it stores FP32, else an
+    // FP32 volume of its own (allocated once)
+    float *cost = (float *)c->vol_l;
     if (p.vol_dtype != SR_VOL_F32) {
-        if (!c->g_vol) {
-            SR_TRY(c, dalloc(&c->g_vol, 2 * npx * D), "cudaMalloc(grad volumes)");
-        }
+        if (!c->g_vol) SR_TRY(c, dalloc(&c->g_vol, npx * D), "cudaMalloc(grad volume)");
         cost = c->g_vol;
-        G = c->g_vol + npx * D;
     }
     cudaStream_t st = c->st;
     c->matched = false;   // the context's scratch no longer holds the last sr_match
@@ -454,7 +451,7 @@ sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right
     double *out3 = c->g_partial + nparts;
     SR_TRY(c, sr::launch_grad(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, p.agg_radius,
                               p.gamma_d, p.gamma_r, c->alpha0, c->alpha1, c->delta, c->rw, c->mu_l,
-                              c->inv_l, c->mu_r, c->inv_r, cost, d_dstar, c->g_wsum, G,
+                              c->inv_l, c->mu_r, c->inv_r, cost, d_dstar, c->g_wsum,
                               d_grad_right ? c->g_rw : nullptr, d_grad_left, d_grad_right,
                               c->g_partial, out3, st),
            "grad");

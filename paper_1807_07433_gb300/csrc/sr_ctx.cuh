@@ -34,7 +34,7 @@ struct sr_ctx {
     char err[256] = {0};
     SrBatch *batch = nullptr;        // batched-form resources (sr_batch.cu), on first use
     // sr_grad_plane scratch, on first use: wsum and grw [H*W], FP64 partials and,
-    // for 16-bit cost volumes, FP32 cost and G volumes [2][H*W*D]
+    // for 16-bit cost volumes, an FP32 reference volume [H*W*D]
     float *g_vol = nullptr, *g_wsum = nullptr, *g_rw = nullptr;
     double *g_partial = nullptr;     // block partials, then 3 results at the end
 };

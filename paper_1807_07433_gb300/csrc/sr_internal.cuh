@@ -107,16 +107,15 @@ cudaError_t launch_xyz(const float *disp, int W, int H, double f_px, double base
 // Sec. II-A warp) with respect to alpha and the images; rw, the block
 // statistics and cost (the FP32 reference volume [H][W][D]) must hold the
 // warp, Eqs. 4-5 and Eq. 3 at (alpha0, alpha1, delta).
-//   wsum [H*W], G [H*W*D], partial [grad_partial_count(W, H) * 3] doubles: scratch
+//   wsum [H*W], partial [grad_partial_count(W, H) * 3] doubles: scratch
 //   grw, gl, gr: [H*W] FP32 or null (gr needs grw); out3 = {L, dL/dalpha0, dL/dalpha1}
 size_t grad_partial_count(int W, int H);
 cudaError_t launch_grad(const uint8_t *left, const uint8_t *right, int pitch, int W, int H, int D,
                         int ncc_r, int agg_r, float gamma_d, float gamma_r, double alpha0,
                         double alpha1, double delta, const float *rw, const float *mu_l,
                         const float *inv_l, const float *mu_r, const float *inv_r,
-                        const float *cost, const int16_t *dstar, float *wsum, float *G,
-                        float *grw, float *gl, float *gr, double *partial, double *out3,
-                        cudaStream_t st);
+                        const float *cost, const int16_t *dstar, float *wsum, float *grw,
+                        float *gl, float *gr, double *partial, double *out3, cudaStream_t st);
 
 __host__ __device__ inline int clampi(int x, int lo, int hi) {
     return x < lo ? lo : (x > hi ? hi : x);

@@ -196,3 +196,20 @@ def test_match_after_grad_is_unchanged():
         got = m.match(dl, dr).cpu().numpy()
     assert np.array_equal(np.isnan(got), np.isnan(ref))
     assert np.array_equal(got[~np.isnan(got)], ref[~np.isnan(ref)])
+
+
+def test_full_size_crop_matches_oracle():
+    """1280x720 D64 NCC 7x7 bilateral 11x11 scene, the adjoint restricted to
+    the crop rows 560-679, cols 560-719 (low in the frame, where alpha1
+    matters), at the true plane perturbed by (U[-1.5, 1.5], U[-0.01, 0.01])
+    with seed 5: L, dL/dalpha and the image gradients against the oracle,
+    which evaluates only the pixels of the set."""
+    w = synth.C2
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    dstar = np.full((H, W), -1, np.int16)
+    dstar[560:680, 560:720] = int(w.delta)
+    rng = np.random.default_rng(5)
+    a0 = w.scene.alpha0 + rng.uniform(-1.5, 1.5)
+    a1 = w.scene.alpha1 + rng.uniform(-0.01, 0.01)
+    _check(w, left, right, dstar, a0, a1)
