@@ -167,22 +167,22 @@ typedef struct {
     int16_t *d_wta_or_null;     /* optional, width x height */
 } sr_pair_desc;
 
-/* The pipeline of sr_match for n pairs of any sizes in one call: each stage
- * is one persistent launch over the flat list of (pair, tile) work items of
- * the whole batch, and the seven stage launches are captured once into a CUDA
- * graph that later calls replay.  The context supplies D, the radii, gamma_d,
- * gamma_r, lr_thresh, vol_dtype and the stream; its width and height are not
- * used.  Scratch for the whole batch (about sum of W*H*(2*D*e + 40) bytes,
- * e as for sr_create) is allocated on first use and grown when a larger batch
+/* The pipeline of sr_match for n pairs of any sizes in one call, captured
+ * into a CUDA graph that later calls replay.  By default each stage is one
+ * persistent launch over the flat list of (pair, tile) work items of the
+ * whole batch; sr_set_batch_schedule and sr_set_autotune select among
+ * other schedules.  The context supplies D, the radii, gamma_d, gamma_r,
+ * lr_thresh, vol_dtype and the stream; its width and height are not used.
+ * Scratch for the whole batch (about sum of W*H*(2*D*e + 40) bytes, e as
+ * for sr_create) is allocated on first use and grown when a larger batch
  * arrives.  Results are identical to n sr_match calls.  Asynchronous.
  * Errors: SR_ERR_INVALID_ARG (n < 1, a bad pair), SR_ERR_OOM, SR_ERR_CUDA. */
 sr_status sr_match_batch(sr_ctx *ctx, int n, const sr_pair_desc *pairs);
 
 /* Autotuning of sr_match_batch.  With enable != 0, the first batch of each
  * shape (multiset of image sizes, D, radii, volume type, GPU) times the
- * candidate schedules -- grid factor 1 or 2 of the persistent NCC and
- * aggregation launches, caller's pair order or largest pair first -- on the
- * caller's data and keeps the fastest.  cache_path (nullable) names a file of
+ * eight candidate schedules of sr_set_batch_schedule on the caller's data
+ * and keeps the fastest.  cache_path (nullable) names a file of
  * one JSON object per line that stores the choices across processes;
  * unreadable lines are skipped (defaults used) and reported by
  * sr_last_error.  Disabled: grid factor 1, caller's order. */
@@ -190,9 +190,12 @@ sr_status sr_set_autotune(sr_ctx *ctx, int enable, const char *cache_path);
 
 /* Fix the schedule of sr_match_batch instead of tuning it: 0-3 one
  * persistent launch per stage (bit 0: two waves of CTAs instead of one;
- * bit 1: largest pair first), 4 / 5 per-pair launches on 4 / 8 streams of
- * the graph, largest pair first; -1 restores the automatic choice.
- * SR_ERR_INVALID_ARG for other values. */
+ * bit 1: largest pair first); 4 / 5 per-pair launches of the
+ * descriptor-driven kernels on 4 / 8 streams of the graph, largest pair
+ * first; 6 / 7 per-pair launches of the kernels of sr_match on 1 / 4 streams,
+ * largest pair first (the graph holds the pairs' pointers and planes, and is
+ * re-captured and updated in place when they change); -1 restores the
+ * automatic choice.  SR_ERR_INVALID_ARG for other values. */
 sr_status sr_set_batch_schedule(sr_ctx *ctx, int variant);
 
 /* One-line JSON description of the schedule of the last sr_match_batch. */

@@ -378,22 +378,28 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const AggSmem<R, D, VT> sm{smem_raw};
     agg_init_barriers(sm);
-    int &s_t = *sm.next_slot();
-    const int *st = stage_start(sm.start(), start, n);
+    // The loop state lives in shared memory and is re-read after each tile,
+    // so that none of it occupies registers while a tile runs (the tile
+    // needs all 128).  s_state[0]: current work item, s_state[1]: its pair.
+    int *s_state = sm.next_slot();
+    stage_start(sm.start(), start, n);
+    if (threadIdx.x == 0) { s_state[0] = -1; s_state[1] = 0; }
     unsigned ph = 0;
-    const int total = st[n];
-    int p = 0;
-    for (int t = blockIdx.x;; ) {
+    for (;;) {
         // next work item: in order from a counter (keeps the tiles in flight a
         // contiguous band, so halo rows are shared through L2), or strided
         __syncthreads();   // the previous tile's epilogue is done with shared memory
-        if (next) {
-            if (threadIdx.x == 0) s_t = atomicAdd(next, 1);
-            __syncthreads();
-            t = s_t;
+        if (threadIdx.x == 0) {
+            const int *st = n + 1 <= kStartSmem ? sm.start() : start;
+            const int prev = s_state[0];
+            const int t = next ? atomicAdd(next, 1) : (prev < 0 ? (int)blockIdx.x : prev + (int)gridDim.x);
+            s_state[0] = t;
+            s_state[1] = t < st[n] ? find_pair(st, n, t, s_state[1]) : -1;
         }
-        if (t >= total) break;
-        p = find_pair(st, n, t, p);
+        __syncthreads();
+        const int t = s_state[0], p = s_state[1];
+        if (p < 0) break;
+        const int *st = n + 1 <= kStartSmem ? sm.start() : start;
         const PairDesc &P = pairs[p];
         const int tl = t - st[p], tx = (P.W + kAggTX - 1) / kAggTX;
         agg_tile<R, D, !TARGET, VT>(sm, ph, static_cast<const VT *>(TARGET ? P.vol_r : P.vol_l),
@@ -401,7 +407,6 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
                                     P.W, P.H, kd, kr, TARGET ? P.lbl_r : P.lbl_l,
                                     TARGET ? nullptr : P.dsub, nullptr, err, wait_cycles, 0,
                                     (tl % tx) * kAggTX, (tl / tx) * kAggTY);
-        if (!next) t += gridDim.x;
     }
 }
 

@@ -19,7 +19,12 @@
 //     (one CTA per tile, as sr_match), the pairs spread over 4 or 8 forked
 //     capture streams, largest first, so that one pair's kernels fill the
 //     tails of another's; still descriptor-driven, so the graph replays with
-//     new images and planes as long as the sequence of sizes repeats.
+//     new images and planes as long as the sequence of sizes repeats;
+//   C (variants 6-7): per pair, the eight kernels of sr_match itself with the
+//     pair's pointers and plane as kernel parameters, on 1 or 4 forked capture
+//     streams, largest first.  The graph holds the parameters, so a call with
+//     other pointers or planes re-captures it and updates the executable graph
+//     in place (cudaGraphExecUpdate; a fresh instantiation if that fails).
 // The tuner times each candidate on the caller's own batch the first time a
 // batch shape is seen and keeps the fastest; with a cache path the choice is
 // stored as one JSON object per line, keyed by GPU name, method parameters
@@ -41,11 +46,14 @@
 namespace {
 
 constexpr int kBatchStages = 3;     // tile lists: 32x8 pixels, 32x8 stats, 32x4 NCC/agg
-constexpr int kVariants = 6;        // 0-3: schedule A (bit 0: f = 2; bit 1: largest first)
+constexpr int kVariants = 8;        // 0-3: schedule A (bit 0: f = 2; bit 1: largest first)
                                     // 4, 5: schedule B on 4 / 8 streams, largest first
-constexpr int kMaxSide = 8;         // capture streams of schedule B
-inline bool sched_b(int v) { return v >= 4; }
-inline int sched_b_streams(int v) { return v == 4 ? 4 : 8; }
+                                    // 6, 7: schedule C on 1 / 4 streams, largest first
+constexpr int kMaxSide = 8;         // capture streams of schedules B and C
+inline bool sched_b(int v) { return v == 4 || v == 5; }
+inline bool sched_c(int v) { return v >= 6; }
+inline bool per_pair(int v) { return v >= 4; }
+inline int pair_streams(int v) { return v == 4 ? 4 : v == 5 ? 8 : v == 6 ? 1 : 4; }
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -69,12 +77,13 @@ struct SrBatch {
     int graph_n = -1, graph_variant = -1;
     std::vector<int> tiles_pix, tiles_stat, tiles_t4;     // staged order
     std::vector<long long> graph_sizes;                   // size sequence the graph was built for
+    std::vector<sr::PairDesc> graph_desc;                 // descriptors a schedule-C graph holds
     bool tune = false;
     std::string cache_path;
     std::map<std::string, int> tuned;
     int variant = 0;
     int forced = -1;                          // sr_set_batch_schedule, -1 = automatic
-    float tune_ms[kVariants] = {0, 0, 0, 0, 0, 0};
+    float tune_ms[kVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
     bool cache_bad = false;
     int sms = 0;
 };
@@ -152,8 +161,9 @@ void append_cache(SrBatch *b, const std::string &key, int v, const float *ms) {
     if (b->cache_path.empty()) return;
     FILE *f = fopen(b->cache_path.c_str(), "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms\": [%.4f, %.4f, %.4f, %.4f, %.4f, %.4f]}\n",
-            key.c_str(), v, ms[0], ms[1], ms[2], ms[3], ms[4], ms[5]);
+    fprintf(f, "{\"key\": \"%s\", \"variant\": %d, \"ms\": [", key.c_str(), v);
+    for (int i = 0; i < kVariants; ++i) fprintf(f, i ? ", %.4f" : "%.4f", ms[i]);
+    fprintf(f, "]}\n");
     fclose(f);
 }
 
@@ -199,18 +209,45 @@ cudaError_t launch_pair(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     return sr::launch_lrc_post_batch(d, ps, 1, p.lr_thresh, tp, st);
 }
 
+// Schedule C: the kernels of sr_match for pair k, parameters from the host
+// copy of its descriptor.
+cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
+    const sr_params &p = c->p;
+    const int D = p.max_disp;
+    const sr::PairDesc &P = b->h_desc[k];
+    const sr::AggDebug dbg = agg_debug(c);
+    cudaError_t e;
+    if ((e = sr::launch_warp(P.right, P.pitch, P.W, P.H, P.alpha0, P.alpha1, P.delta, P.rw, st)) != cudaSuccess) return e;
+    if ((e = sr::launch_stats(P.left, P.pitch, P.rw, P.W, P.H, D, p.ncc_radius, P.mu_l, P.inv_l,
+                              P.mu_r, P.inv_r, st)) != cudaSuccess) return e;
+    if ((e = sr::launch_ncc(false, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
+                            P.H, D, p.ncc_radius, P.vol_l, p.vol_dtype, st)) != cudaSuccess) return e;
+    if ((e = sr::launch_ncc(true, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
+                            P.H, D, p.ncc_radius, P.vol_r, p.vol_dtype, st)) != cudaSuccess) return e;
+    if ((e = sr::launch_agg(P.vol_l, p.vol_dtype, P.left, P.pitch, nullptr, P.W, P.H, D,
+                            p.agg_radius, p.gamma_d, p.gamma_r, P.lbl_l, P.dsub, nullptr, dbg,
+                            st)) != cudaSuccess) return e;
+    if ((e = sr::launch_agg(P.vol_r, p.vol_dtype, nullptr, 0, P.rw, P.W, P.H, D, p.agg_radius,
+                            p.gamma_d, p.gamma_r, P.lbl_r, nullptr, nullptr, dbg, st)) != cudaSuccess) return e;
+    return sr::launch_lrc_post(P.lbl_l, P.lbl_r, P.dsub, P.W, P.H, P.alpha0, P.alpha1, P.delta,
+                               p.lr_thresh, P.disp, P.wta, st);
+}
+
 cudaError_t launch_stages(sr_ctx *c, SrBatch *b, int n, int variant, cudaStream_t st) {
     const sr_params &p = c->p;
     const int D = p.max_disp;
     cudaError_t e;
-    if (sched_b(variant)) {
+    if (per_pair(variant)) {
         // fork the pairs over S streams, join back into st
-        const int S = sched_b_streams(variant);
+        const int S = pair_streams(variant);
         if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
         for (int i = 0; i < S; ++i)
             if ((e = cudaStreamWaitEvent(b->side[i], b->fork, 0)) != cudaSuccess) return e;
-        for (int k = 0; k < n; ++k)
-            if ((e = launch_pair(c, b, k, b->side[k % S])) != cudaSuccess) return e;
+        for (int k = 0; k < n; ++k) {
+            e = sched_c(variant) ? launch_pair_direct(c, b, k, b->side[k % S])
+                                 : launch_pair(c, b, k, b->side[k % S]);
+            if (e != cudaSuccess) return e;
+        }
         for (int i = 0; i < S; ++i) {
             if ((e = cudaEventRecord(b->join[i], b->side[i])) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(st, b->join[i], 0)) != cudaSuccess) return e;
@@ -244,7 +281,7 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
     const int D = p.max_disp;
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    if ((variant & 2) || sched_b(variant))
+    if ((variant & 2) || per_pair(variant))
         std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
             return (long long)pairs[a].width * pairs[a].height >
                    (long long)pairs[b2].width * pairs[b2].height;
@@ -312,7 +349,6 @@ std::vector<long long> size_signature(const SrBatch *b, int n) {
 }
 
 cudaError_t capture_graph(sr_ctx *c, SrBatch *b, int n, int variant) {
-    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -320,13 +356,34 @@ cudaError_t capture_graph(sr_ctx *c, SrBatch *b, int n, int variant) {
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (el != cudaSuccess) { if (g) cudaGraphDestroy(g); return el; }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&b->graph, g, 0);
+    bool updated = false;
+    if (b->graph && b->graph_n == n && b->graph_variant == variant) {
+        // same kernels in the same order, other parameters: update in place
+        cudaGraphExecUpdateResultInfo info{};
+        updated = cudaGraphExecUpdate(b->graph, g, &info) == cudaSuccess;
+        if (!updated) cudaGetLastError();
+    }
+    if (!updated) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+    }
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { b->graph = nullptr; return e; }
     b->graph_n = n;
     b->graph_variant = variant;
     b->graph_sizes = size_signature(b, n);
+    b->graph_desc.assign(b->h_desc, b->h_desc + n);
     return cudaSuccess;
+}
+
+// Whether the executable graph must be (re)built for this call's staged batch.
+bool graph_stale(const SrBatch *b, int n, int variant) {
+    if (!b->graph || b->graph_n != n || b->graph_variant != variant) return true;
+    if (sched_b(variant) && b->graph_sizes != size_signature(b, n)) return true;
+    if (sched_c(variant))
+        return b->graph_desc.size() != (size_t)n ||
+               memcmp(b->graph_desc.data(), b->h_desc, n * sizeof(sr::PairDesc)) != 0;
+    return false;
 }
 
 }  // namespace
@@ -422,9 +479,7 @@ sr_status sr_match_batch(sr_ctx *c, int n, const sr_pair_desc *pairs) {
         }
     }
     SR_TRY(c, stage_batch(c, b, n, pairs, variant, c->st), "stage");
-    if (!b->graph || b->graph_n != n || b->graph_variant != variant ||
-        (sched_b(variant) && b->graph_sizes != size_signature(b, n)))
-        SR_TRY(c, capture_graph(c, b, n, variant), "graph capture");
+    if (graph_stale(b, n, variant)) SR_TRY(c, capture_graph(c, b, n, variant), "graph capture");
     SR_TRY(c, cudaGraphLaunch(b->graph, c->st), "cudaGraphLaunch");
     b->variant = variant;
     return SR_OK;
@@ -445,19 +500,24 @@ sr_status sr_batch_info(sr_ctx *c, char *buf, size_t size) {
     if (!c->batch || c->batch->graph_n < 0) return SR_ERR_STATE;
     const SrBatch *b = c->batch;
     const int D = c->p.max_disp;
+    const char *sched = sched_c(b->variant)   ? "per-pair-direct"
+                        : sched_b(b->variant) ? "per-pair-streams"
+                                              : "persistent";
+    char ms[160];
+    int o = 0;
+    for (int i = 0; i < kVariants; ++i)
+        o += snprintf(ms + o, sizeof(ms) - o, i ? ", %.4f" : "%.4f", b->tune_ms[i]);
     snprintf(buf, size,
              "{\"pairs\": %d, \"variant\": %d, \"schedule\": \"%s\", \"grid_factor\": %d, "
              "\"largest_first\": %d, \"streams\": %d, \"kernels\": %d, "
              "\"ncc_ctas_per_sm\": %d, \"agg_ctas_per_sm\": %d, \"sms\": %d, "
-             "\"tune_ms\": [%.4f, %.4f, %.4f, %.4f, %.4f, %.4f], \"scratch_bytes\": %zu}",
-             b->graph_n, b->variant, sched_b(b->variant) ? "per-pair-streams" : "persistent",
-             sched_b(b->variant) ? 1 : ((b->variant & 1) ? 2 : 1),
-             sched_b(b->variant) ? 1 : (b->variant >> 1) & 1,
-             sched_b(b->variant) ? sched_b_streams(b->variant) : 1,
-             sched_b(b->variant) ? 7 * b->graph_n : 7,
+             "\"tune_ms\": [%s], \"scratch_bytes\": %zu}",
+             b->graph_n, b->variant, sched, per_pair(b->variant) ? 1 : ((b->variant & 1) ? 2 : 1),
+             per_pair(b->variant) ? 1 : (b->variant >> 1) & 1,
+             per_pair(b->variant) ? pair_streams(b->variant) : 1,
+             sched_c(b->variant) ? 8 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
              sr::ncc_batch_occupancy(D, c->p.ncc_radius, c->p.vol_dtype),
-             sr::agg_batch_occupancy(D, c->p.agg_radius, c->p.vol_dtype), b->sms, b->tune_ms[0],
-             b->tune_ms[1], b->tune_ms[2], b->tune_ms[3], b->tune_ms[4], b->tune_ms[5],
+             sr::agg_batch_occupancy(D, c->p.agg_radius, c->p.vol_dtype), b->sms, ms,
              b->pool_bytes);
     return SR_OK;
 }

@@ -84,7 +84,7 @@ def test_batch_equals_single_calls_and_replays(vt):
         assert info["pairs"] == len(SIZES) and info["schedule"] == "persistent"
 
 
-@pytest.mark.parametrize("variant", [1, 2, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 4, 5, 6, 7])
 def test_every_schedule_equals_single_calls(variant):
     from paper_1807_07433_gb300 import sr
     p1, p2 = _pairs(500), _pairs(600)
@@ -94,9 +94,10 @@ def test_every_schedule_equals_single_calls(variant):
         _same(_batch(m.ctx, p2, order=[2, 0, 1, 5, 4, 3]), _single(p2, 0))
         info = sr.sr_batch_info(m.ctx)
         assert info["variant"] == variant
-        assert info["schedule"] == ("per-pair-streams" if variant >= 4 else "persistent")
+        assert info["schedule"] == ("per-pair-direct" if variant >= 6 else
+                                    "per-pair-streams" if variant >= 4 else "persistent")
         with pytest.raises(sr.SrError):
-            sr.sr_set_batch_schedule(m.ctx, 6)
+            sr.sr_set_batch_schedule(m.ctx, 8)
 
 
 def test_autotune_cache_round_trip(tmp_path):
@@ -109,7 +110,7 @@ def test_autotune_cache_round_trip(tmp_path):
         _same(_batch(m.ctx, p), want)
         info = sr.sr_batch_info(m.ctx)
         assert min(info["tune_ms"]) > 0.0          # every candidate was timed
-        assert len(info["tune_ms"]) == 6
+        assert len(info["tune_ms"]) == 8
     lines = open(cache).read().splitlines()
     assert len(lines) == 1 and '"variant": %d' % info["variant"] in lines[0]
     with _ctx() as m:                               # a new context reuses the choice
