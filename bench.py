@@ -567,6 +567,104 @@ def adjoint_report(steps: int, warmup: int):
     return out
 
 
+def sweep_report(steps: int, warmup: int):
+    """Runtime of sr_match at 1280x720, D = 64 for every NCC radius 1..5 and
+    bilateral radius 1..7 (the parameters Fig. 4 varies), same scene and
+    gamma_d / gamma_r as the benchmark; median over steps CUDA-event timings
+    (L2 flushed between steps) plus the per-stage split."""
+    import torch
+
+    from paper_1807_07433_gb300 import sr, synth
+    w = synth.C2
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    dl, dr = torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)
+    disp = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for ncc_r in range(1, 6):
+        for agg_r in range(1, 8):
+            with sr.Matcher(W, H, w.D, ncc_r, agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                            stream=stream) as m:
+                m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+                for _ in range(warmup):
+                    m.match(dl, dr, disp)
+                sr.sr_set_profiling(m.ctx, True)
+                ms, st_rows = [], []
+                for _ in range(steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.match(dl, dr, disp)
+                    e1.record(stream)
+                    st_rows.append(sr.sr_stage_times(m.ctx))
+                    ms.append(e0.elapsed_time(e1))
+                t = statistics.median(ms)
+                valid = float(torch.isfinite(disp).float().mean())
+            rows.append({"ncc_window": 2 * ncc_r + 1, "bilateral_window": 2 * agg_r + 1,
+                         "ms": round(t, 4), "mdes": round(mdes(W, H, w.D, t * 1e-3), 1),
+                         "fps": round(1000.0 / t, 1),
+                         "ncc_ms": round(statistics.median(r["ncc_ref"] + r["ncc_tgt"] for r in st_rows), 4),
+                         "agg_ms": round(statistics.median(r["agg_ref"] + r["agg_tgt"] for r in st_rows), 4),
+                         "valid_fraction": round(valid, 4)})
+    return {"report": "sweep", "workload": w.name, "W": W, "H": H, "D": w.D, "steps": steps,
+            "warmup": warmup, "rows": rows}
+
+
+def fit_report(steps: int, warmup: int):
+    """Sec. II-A plane fitting on the benchmark frame: time of sr_fit_alpha
+    (256 RANSAC hypotheses, tau = 0.5 px) and sr_fit_roll (near-field patch
+    rows 560-719, columns 320-959) on the disparity map of sr_match, the
+    fitted plane against the scene's, and the closed loop match -> fit ->
+    match from a perturbed plane."""
+    import numpy as np
+    import torch
+
+    from paper_1807_07433_gb300 import sr, synth
+    w = synth.C2
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    dl, dr = torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)
+    pairs = np.random.default_rng(9).integers(0, H * W, size=(256, 2)).astype(np.int32)
+    out = {"report": "fit", "workload": w.name, "hypotheses": 256, "tau_px": 0.5,
+           "roll_patch": [320, 560, 960, 720], "steps": steps, "warmup": warmup}
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=stream) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        disp = m.match(dl, dr)
+
+        def timed(fn):
+            for _ in range(warmup):
+                fn()
+            ts = []
+            for _ in range(steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = fn()
+                ts.append(time.perf_counter() - t0)
+            return r, statistics.median(ts) * 1e3
+        fa, ms_a = timed(lambda: sr.sr_fit_alpha(m.ctx, disp, pairs, 0.5))
+        fr, ms_r = timed(lambda: sr.sr_fit_roll(m.ctx, disp, 320, 560, 960, 720))
+        out.update({"fit_alpha_ms": round(ms_a, 3), "fit_roll_ms": round(ms_r, 3),
+                    "alpha": fa["alpha"].tolist(), "alpha_true": [w.scene.alpha0, w.scene.alpha1],
+                    "inliers": fa["n_inliers"], "valid_pixels": int(torch.isfinite(disp).sum()),
+                    "gamma": fr[0].tolist(), "roll_rad": fr[1], "roll_pixels": fr[2]})
+        loop = []
+        a = (w.scene.alpha0 + 1.3, w.scene.alpha1 - 0.004)
+        for it in range(3):
+            m.set_plane(a[0], a[1], w.delta)
+            d = m.match(dl, dr)
+            a = tuple(sr.sr_fit_alpha(m.ctx, d, pairs, 0.5)["alpha"])
+            loop.append({"iteration": it + 1, "alpha": list(a),
+                         "err_px": [a[0] - w.scene.alpha0, (a[1] - w.scene.alpha1) * (H - 1)]})
+        out["loop_from_perturbed"] = loop
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,7 +672,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--report", choices=("precision", "batch", "adjoint"), default=None,
+    ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit"), default=None,
                     help="print a report instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -587,6 +685,12 @@ def main():
         return
     if args.report == "adjoint":
         print(json.dumps(adjoint_report(args.steps, args.warmup)), flush=True)
+        return
+    if args.report == "sweep":
+        print(json.dumps(sweep_report(args.steps, args.warmup)), flush=True)
+        return
+    if args.report == "fit":
+        print(json.dumps(fit_report(args.steps, args.warmup)), flush=True)
         return
     from paper_1807_07433_gb300 import synth
     w = synth.C2

@@ -235,6 +235,36 @@ sr_status sr_reconstruct(sr_ctx *ctx, const float *d_disp, float *d_xyz);
  * sr_match are no longer available to sr_get_buffer afterwards); the first
  * call allocates about 12*W*H bytes more, plus 4*W*H*D bytes for an FP32
  * cost volume when the context stores 16-bit volumes. */
+/* Road-plane fitting from a disparity map, Sec. II-A: the paper fits alpha
+ * of Eq. 2 by least squares with RANSAC on reliable correspondences, and the
+ * roll angle by fitting a plane to a near-field patch of the disparity map.
+ * Here the correspondences are the valid pixels of a full-disparity map
+ * (d_disp, W x H float as written by sr_match, NaN = rejected), so that the
+ * plane of the next frame can come from this frame's result.
+ *
+ * sr_fit_alpha: RANSAC over n_hyp caller-drawn point pairs
+ *   h_pairs[2h], h_pairs[2h+1] (pixel indices v*W+u, host memory;
+ *   1 <= n_hyp <= 65536).  Hypothesis h is the line d = a0 + a1 v through its
+ *   two points, computed in double and rounded to float; it has no model
+ *   if a point is out of range or NaN, or both lie on one row.  Its inliers
+ *   are the valid pixels with |d - (a0 + a1 v)| <= tau_px, decided in single
+ *   precision (one fused multiply-add, then one subtraction).  The hypothesis
+ *   with the most inliers wins (ties: the smallest h).  h_alpha (host
+ *   double[2]) receives the least-squares line through its inliers
+ *   (normal equations, FP64 sums).  Optional outputs: h_counts (int32[n_hyp],
+ *   -1 for no model), h_best, h_n_inliers.  Synchronises the stream.
+ *   SR_ERR_STATE if no hypothesis has a model or the inliers span one row.
+ * sr_fit_roll: least-squares plane d = g0 + g1 u + g2 v over the valid
+ *   pixels of the patch [u_lo, u_hi) x [v_lo, v_hi) (clipped to the image),
+ *   h_gamma = (g0, g1, g2), *h_roll = atan(-g1 / g2) in radians, *h_n (nullable)
+ *   the pixels used.  Synchronises the stream.  SR_ERR_INVALID_ARG for an
+ *   empty patch, SR_ERR_STATE if the normal equations are singular. */
+sr_status sr_fit_alpha(sr_ctx *ctx, const float *d_disp, int n_hyp, const int32_t *h_pairs,
+                       float tau_px, double *h_alpha, int32_t *h_counts, int *h_best,
+                       int *h_n_inliers);
+sr_status sr_fit_roll(sr_ctx *ctx, const float *d_disp, int u_lo, int v_lo, int u_hi, int v_hi,
+                      double *h_gamma, double *h_roll, int *h_n);
+
 sr_status sr_grad_plane(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                         int pitch_bytes, const int16_t *d_dstar, double *h_out3,
                         float *d_grad_left, float *d_grad_right);

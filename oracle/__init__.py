@@ -91,6 +91,8 @@ def _load():
                                          vp, vp, vp]),
                 "orc_objective": (d, [pp, vp, vp, vp]),
                 "orc_grad": (i, [pp, vp, vp, vp, vp, vp, vp, vp]),
+                "orc_fit_alpha": (i, [vp, i, i, i, vp, ctypes.c_float, vp, vp, vp]),
+                "orc_fit_roll": (i, [vp, i, i, i, i, i, i, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -317,3 +319,37 @@ def grad(p: Params, left, right, dstar):
     if rc != 0:
         raise RuntimeError(f"orc_grad failed with {rc}")
     return out_l.value, da, gl, gr
+
+
+@dataclass
+class AlphaFit:
+    best: int                 # index of the best hypothesis, -1 if none
+    counts: np.ndarray        # inliers per hypothesis, -1 without a model
+    alpha: np.ndarray         # least-squares (alpha0, alpha1) through the best's inliers
+    n_inliers: int
+
+
+def fit_alpha(disp: np.ndarray, pairs: np.ndarray, tau: float) -> AlphaFit:
+    """Sec. II-A: alpha by least squares with RANSAC over the given point
+    pairs (pixel indices v*W+u) of a full-disparity map (NaN = rejected)."""
+    d = np.ascontiguousarray(disp, dtype=np.float32)
+    H, W = d.shape
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    counts = np.zeros(len(pr), np.int32)
+    alpha = np.full(2, np.nan)
+    n = ctypes.c_int32(0)
+    best = _load().orc_fit_alpha(_ptr(d), W, H, len(pr), _ptr(pr), float(tau), _ptr(counts),
+                                 _ptr(alpha), ctypes.byref(n))
+    return AlphaFit(best, counts, alpha, n.value)
+
+
+def fit_roll(disp: np.ndarray, patch: tuple[int, int, int, int]):
+    """Sec. II-A roll angle: least-squares plane d = g0 + g1 u + g2 v over the
+    valid pixels of patch (u_lo, v_lo, u_hi, v_hi); returns (g[3], roll, n)."""
+    d = np.ascontiguousarray(disp, dtype=np.float32)
+    H, W = d.shape
+    g = np.zeros(3)
+    roll = ctypes.c_double(0.0)
+    n = _load().orc_fit_roll(_ptr(d), W, H, *[int(x) for x in patch], _ptr(g),
+                             ctypes.byref(roll))
+    return g, roll.value, n

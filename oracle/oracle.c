@@ -644,3 +644,111 @@ int orc_grad(const orc_params *p, const double *il, const double *ir, const int3
     free(R); free(dds); free(gR); free(gL);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Road-plane fitting from a disparity map (Sec. II-A): alpha of Eq. 2 by
+ * least squares with RANSAC, and the roll angle from a linear plane fitted
+ * to a near-field patch.  The correspondences are the valid pixels of a
+ * full-disparity map d[H][W] (NaN = rejected) instead of ORB matches.
+ * ------------------------------------------------------------------------ */
+
+/* Two-point model of hypothesis (i1, i2) (pixel indices v*W+u): the line
+ * d = a0 + a1 v through both points, in double.  Returns 0 if either point is
+ * invalid or both lie on one row. */
+static int line_through(const float *disp, int W, int i1, int i2, double *a0, double *a1) {
+    const double d1 = disp[i1], d2 = disp[i2];
+    const int v1 = i1 / W, v2 = i2 / W;
+    if (isnan(d1) || isnan(d2) || v1 == v2) return 0;
+    *a1 = (d2 - d1) / (double)(v2 - v1);
+    *a0 = d1 - *a1 * (double)v1;
+    return 1;
+}
+
+/* Inlier test of pixel (v, d) against a model, decided in single precision:
+ * |d - fma(a1, v, a0)| <= tau with a0, a1 rounded to float (the precision of
+ * the disparity map itself). */
+static int is_inlier(float d, int v, float a0f, float a1f, float tau) {
+    return !isnan(d) && fabsf(d - fmaf(a1f, (float)v, a0f)) <= tau;
+}
+
+/* RANSAC over n_hyp given point pairs (pairs[2h], pairs[2h+1]): counts[h] =
+ * inliers of hypothesis h (-1 if it has no model); the best hypothesis has
+ * the most inliers (ties: the smallest h); alpha = least-squares line through
+ * its inliers (normal equations in double).  Returns the best h, or -1 if no
+ * hypothesis has a model or the inliers span fewer than two rows. */
+int orc_fit_alpha(const float *disp, int W, int H, int n_hyp, const int32_t *pairs, float tau,
+                  int32_t *counts, double *alpha, int32_t *n_inliers) {
+    const size_t npx = (size_t)W * H;
+    int best = -1, best_n = -1;
+    for (int h = 0; h < n_hyp; ++h) {
+        double a0, a1;
+        const int i1 = pairs[2 * h], i2 = pairs[2 * h + 1];
+        if (i1 < 0 || i2 < 0 || (size_t)i1 >= npx || (size_t)i2 >= npx ||
+            !line_through(disp, W, i1, i2, &a0, &a1)) {
+            counts[h] = -1;
+            continue;
+        }
+        const float a0f = (float)a0, a1f = (float)a1;
+        int32_t c = 0;
+        for (size_t i = 0; i < npx; ++i) c += is_inlier(disp[i], (int)(i / W), a0f, a1f, tau);
+        counts[h] = c;
+        if (c > best_n) { best_n = c; best = h; }
+    }
+    if (n_inliers) *n_inliers = best_n < 0 ? 0 : best_n;
+    if (best < 0) return -1;
+    double a0, a1;
+    line_through(disp, W, pairs[2 * best], pairs[2 * best + 1], &a0, &a1);
+    const float a0f = (float)a0, a1f = (float)a1;
+    double s0 = 0, s1 = 0, s2 = 0, t0 = 0, t1 = 0;   /* n, sum v, sum v^2, sum d, sum v d */
+    for (size_t i = 0; i < npx; ++i) {
+        const int v = (int)(i / W);
+        if (!is_inlier(disp[i], v, a0f, a1f, tau)) continue;
+        const double d = disp[i];
+        s0 += 1.0; s1 += v; s2 += (double)v * v; t0 += d; t1 += (double)v * d;
+    }
+    const double det = s0 * s2 - s1 * s1;
+    if (det == 0.0) return -1;
+    alpha[1] = (s0 * t1 - s1 * t0) / det;
+    alpha[0] = (t0 - alpha[1] * s1) / s0;
+    return best;
+}
+
+/* Roll: least-squares plane d = g0 + g1 u + g2 v over the valid pixels of the
+ * patch [u_lo, u_hi) x [v_lo, v_hi); gamma = atan(-g1 / g2).  Solves the 3x3
+ * normal equations by Gaussian elimination with partial pivoting.  Returns
+ * the number of pixels used, or -1 if the system is singular. */
+int orc_fit_roll(const float *disp, int W, int H, int u_lo, int v_lo, int u_hi, int v_hi,
+                 double *g, double *roll) {
+    double A[3][4] = {{0}};
+    int n = 0;
+    for (int v = v_lo < 0 ? 0 : v_lo; v < v_hi && v < H; ++v)
+        for (int u = u_lo < 0 ? 0 : u_lo; u < u_hi && u < W; ++u) {
+            const float df = disp[(size_t)v * W + u];
+            if (isnan(df)) continue;
+            const double x[3] = {1.0, (double)u, (double)v}, d = df;
+            for (int r = 0; r < 3; ++r) {
+                for (int c = 0; c < 3; ++c) A[r][c] += x[r] * x[c];
+                A[r][3] += x[r] * d;
+            }
+            ++n;
+        }
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return -1;
+        if (piv != c)
+            for (int k = 0; k < 4; ++k) { const double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+        for (int r = c + 1; r < 3; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    for (int r = 2; r >= 0; --r) {
+        double s = A[r][3];
+        for (int k = r + 1; k < 3; ++k) s -= A[r][k] * g[k];
+        g[r] = s / A[r][r];
+    }
+    *roll = atan(-g[1] / g[2]);
+    return n;
+}

@@ -5,7 +5,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/sr.h"
 #include "sr_ctx.cuh"
@@ -176,7 +178,8 @@ cudaError_t dalloc(T **p, size_t n) {
 void free_all(sr_ctx *c) {
     void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
                     c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
-                    c->stage_disp, c->d_err, c->g_vol, c->g_wsum, c->g_rw, c->g_partial};
+                    c->stage_disp, c->d_err, c->g_vol, c->g_wsum, c->g_rw, c->g_partial,
+                    c->f_pairs, c->f_has, c->f_counts, c->f_model, c->f_partial};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)
@@ -458,6 +461,108 @@ sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right
     SR_TRY(c, cudaMemcpyAsync(h_out3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st),
            "D2H grad");
     SR_TRY(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return take_device_error(c);
+}
+
+sr_status sr_fit_alpha(sr_ctx *c, const float *d_disp, int n_hyp, const int32_t *h_pairs,
+                       float tau_px, double *h_alpha, int32_t *h_counts, int *h_best,
+                       int *h_n_inliers) {
+    if (!c || !d_disp || !h_pairs || !h_alpha || n_hyp < 1 || n_hyp > (1 << 16) ||
+        !(tau_px >= 0.0f) || !isfinite(tau_px))
+        return SR_ERR_INVALID_ARG;
+    const int W = c->p.width, H = c->p.height;
+    const int nb = sr::fit_blocks((long long)W * H);
+    if (!c->f_partial) SR_TRY(c, dalloc(&c->f_partial, (size_t)nb * 9 + 9), "cudaMalloc(fit partials)");
+    if (n_hyp > c->fit_cap) {
+        cudaFree(c->f_pairs); cudaFree(c->f_has); cudaFree(c->f_counts); cudaFree(c->f_model);
+        c->f_pairs = c->f_has = c->f_counts = nullptr;
+        c->f_model = nullptr;
+        c->fit_cap = 0;
+        SR_TRY(c, dalloc(&c->f_pairs, 2 * (size_t)n_hyp), "cudaMalloc(fit pairs)");
+        SR_TRY(c, dalloc(&c->f_has, n_hyp), "cudaMalloc(fit)");
+        SR_TRY(c, dalloc(&c->f_counts, n_hyp), "cudaMalloc(fit)");
+        SR_TRY(c, dalloc(&c->f_model, n_hyp), "cudaMalloc(fit)");
+        c->fit_cap = n_hyp;
+    }
+    cudaStream_t st = c->st;
+    SR_TRY(c, cudaMemcpyAsync(c->f_pairs, h_pairs, 2 * (size_t)n_hyp * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st), "H2D pairs");
+    SR_TRY(c, sr::launch_fit_count(d_disp, W, H, c->f_pairs, n_hyp, tau_px, c->f_model, c->f_has,
+                                   c->f_counts, st), "fit count");
+    std::vector<int> counts(n_hyp), has(n_hyp);
+    SR_TRY(c, cudaMemcpyAsync(counts.data(), c->f_counts, n_hyp * sizeof(int), cudaMemcpyDeviceToHost, st), "D2H");
+    SR_TRY(c, cudaMemcpyAsync(has.data(), c->f_has, n_hyp * sizeof(int), cudaMemcpyDeviceToHost, st), "D2H");
+    SR_TRY(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    int best = -1, best_n = -1;
+    for (int h = 0; h < n_hyp; ++h) {
+        if (!has[h]) { counts[h] = -1; continue; }
+        if (counts[h] > best_n) { best_n = counts[h]; best = h; }
+    }
+    if (h_counts) memcpy(h_counts, counts.data(), n_hyp * sizeof(int32_t));
+    if (h_best) *h_best = best;
+    if (h_n_inliers) *h_n_inliers = best_n < 0 ? 0 : best_n;
+    if (best < 0) {
+        snprintf(c->err, sizeof(c->err), "sr_fit_alpha: no hypothesis has a model");
+        return SR_ERR_STATE;
+    }
+    float2 m;
+    SR_TRY(c, cudaMemcpy(&m, c->f_model + best, sizeof(float2), cudaMemcpyDeviceToHost), "D2H model");
+    double *sums = c->f_partial + (size_t)nb * 9;
+    SR_TRY(c, sr::launch_fit_ls(d_disp, W, H, m.x, m.y, tau_px, c->f_partial, sums, st), "fit ls");
+    double s[5];
+    SR_TRY(c, cudaMemcpyAsync(s, sums, sizeof(s), cudaMemcpyDeviceToHost, st), "D2H sums");
+    SR_TRY(c, cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    // normal equations of d = a0 + a1 v: [n sv; sv svv] a = [sd; svd]
+    const double det = s[0] * s[2] - s[1] * s[1];
+    if (det == 0.0) {
+        snprintf(c->err, sizeof(c->err), "sr_fit_alpha: inliers span fewer than two rows");
+        return SR_ERR_STATE;
+    }
+    h_alpha[1] = (s[0] * s[4] - s[1] * s[3]) / det;
+    h_alpha[0] = (s[3] - h_alpha[1] * s[1]) / s[0];
+    return take_device_error(c);
+}
+
+sr_status sr_fit_roll(sr_ctx *c, const float *d_disp, int u_lo, int v_lo, int u_hi, int v_hi,
+                      double *h_gamma, double *h_roll, int *h_n) {
+    if (!c || !d_disp || !h_gamma || !h_roll) return SR_ERR_INVALID_ARG;
+    const int W = c->p.width, H = c->p.height;
+    u_lo = std::max(u_lo, 0); v_lo = std::max(v_lo, 0);
+    u_hi = std::min(u_hi, W); v_hi = std::min(v_hi, H);
+    if (u_lo >= u_hi || v_lo >= v_hi) return SR_ERR_INVALID_ARG;
+    const int nb = sr::fit_blocks((long long)W * H);
+    if (!c->f_partial) SR_TRY(c, dalloc(&c->f_partial, (size_t)nb * 9 + 9), "cudaMalloc(fit partials)");
+    double *sums = c->f_partial + (size_t)nb * 9;
+    SR_TRY(c, sr::launch_roll_sums(d_disp, W, u_lo, v_lo, u_hi, v_hi, c->f_partial, sums, c->st),
+           "roll sums");
+    double s[9];
+    SR_TRY(c, cudaMemcpyAsync(s, sums, sizeof(s), cudaMemcpyDeviceToHost, c->st), "D2H sums");
+    SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+    if (h_n) *h_n = (int)s[0];
+    // normal equations of d = g0 + g1 u + g2 v, Gaussian elimination with
+    // partial pivoting
+    double A[3][4] = {{s[0], s[1], s[2], s[6]}, {s[1], s[3], s[4], s[7]}, {s[2], s[4], s[5], s[8]}};
+    for (int col = 0; col < 3; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 3; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) {
+            snprintf(c->err, sizeof(c->err), "sr_fit_roll: singular patch (too few rows or columns)");
+            return SR_ERR_STATE;
+        }
+        if (piv != col)
+            for (int k = 0; k < 4; ++k) std::swap(A[col][k], A[piv][k]);
+        for (int r = col + 1; r < 3; ++r) {
+            const double f = A[r][col] / A[col][col];
+            for (int k = col; k < 4; ++k) A[r][k] -= f * A[col][k];
+        }
+    }
+    for (int r = 2; r >= 0; --r) {
+        double t = A[r][3];
+        for (int k = r + 1; k < 3; ++k) t -= A[r][k] * h_gamma[k];
+        h_gamma[r] = t / A[r][r];
+    }
+    *h_roll = atan(-h_gamma[1] / h_gamma[2]);
     return take_device_error(c);
 }
 

@@ -37,6 +37,11 @@ struct sr_ctx {
     // for 16-bit cost volumes, an FP32 reference volume [H*W*D]
     float *g_vol = nullptr, *g_wsum = nullptr, *g_rw = nullptr;
     double *g_partial = nullptr;     // block partials, then 3 results at the end
+    // sr_fit_alpha / sr_fit_roll scratch, grown on demand
+    int fit_cap = 0;                 // hypotheses the buffers hold
+    int *f_pairs = nullptr, *f_has = nullptr, *f_counts = nullptr;
+    float2 *f_model = nullptr;
+    double *f_partial = nullptr;     // fit_blocks(W*H) * 9 partials, then 9 sums
 };
 
 namespace {

@@ -117,6 +117,22 @@ cudaError_t launch_grad(const uint8_t *left, const uint8_t *right, int pitch, in
                         const float *cost, const int16_t *dstar, float *wsum, float *grw,
                         float *gl, float *gr, double *partial, double *out3, cudaStream_t st);
 
+// Sec. II-A road-plane fitting from a full-disparity map [H][W] (NaN =
+// rejected).  launch_fit_count: per hypothesis h, the line through pixels
+// pairs[2h], pairs[2h+1] (model[h], has_model[h]) and its inlier count
+// counts[h] (|d - (a0 + a1 v)| <= tau, single precision).  launch_fit_ls:
+// out5 = FP64 {n, sum v, sum v^2, sum d, sum v d} over the inliers of (a0, a1).
+// launch_roll_sums: out9 = FP64 normal-equation sums {n, su, sv, suu, suv,
+// svv, sd, sud, svd} over the valid pixels of [u_lo, u_hi) x [v_lo, v_hi).
+// partial: scratch of fit_blocks(items) * 9 doubles.
+int fit_blocks(long long items);
+cudaError_t launch_fit_count(const float *disp, int W, int H, const int *pairs, int n, float tau,
+                             float2 *model, int *has_model, int *counts, cudaStream_t st);
+cudaError_t launch_fit_ls(const float *disp, int W, int H, float a0, float a1, float tau,
+                          double *partial, double *out5, cudaStream_t st);
+cudaError_t launch_roll_sums(const float *disp, int W, int u_lo, int v_lo, int u_hi, int v_hi,
+                             double *partial, double *out9, cudaStream_t st);
+
 __host__ __device__ inline int clampi(int x, int lo, int hi) {
     return x < lo ? lo : (x > hi ? hi : x);
 }

@@ -28,6 +28,7 @@ SR_DEBUG_WITHHOLD_ROW = 2
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
            "sr_match_host", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
+           "sr_fit_alpha", "sr_fit_roll",
            "sr_get_buffer", "sr_set_debug",
            "sr_set_profiling", "sr_synchronize", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
            "sr_status_str", "sr_last_error", "sr_version")
@@ -88,6 +89,10 @@ def load(path: str | None = None):
                 "sr_set_batch_schedule": (i, [vp, i]),
                 "sr_reconstruct": (i, [vp, vp, vp]),
                 "sr_grad_plane": (i, [vp, vp, vp, i, vp, ctypes.POINTER(d), vp, vp]),
+                "sr_fit_alpha": (i, [vp, vp, i, vp, f, ctypes.POINTER(d), vp,
+                                     ctypes.POINTER(i), ctypes.POINTER(i)]),
+                "sr_fit_roll": (i, [vp, vp, i, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d),
+                                    ctypes.POINTER(i)]),
                 "sr_get_buffer": (i, [vp, i, vp, ctypes.POINTER(sz)]),
                 "sr_set_debug": (i, [vp, i]),
                 "sr_set_profiling": (i, [vp, i]),
@@ -227,6 +232,28 @@ def sr_grad_plane(ctx, d_left, d_right, pitch_bytes: int, d_dstar, d_grad_left=N
                                      _ptr(d_dstar), out, _ptr(d_grad_left), _ptr(d_grad_right)),
            "sr_grad_plane")
     return np.array(out[:], np.float64)
+
+
+def sr_fit_alpha(ctx, d_disp, pairs, tau_px: float) -> dict:
+    """RANSAC + least squares for alpha of Eq. 2; pairs: int [n, 2] pixel indices."""
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    alpha = (ctypes.c_double * 2)()
+    counts = np.zeros(len(pr), np.int32)
+    best, n_in = ctypes.c_int(-1), ctypes.c_int(0)
+    _check(ctx, load().sr_fit_alpha(ctx, _ptr(d_disp), len(pr), pr.ctypes.data, float(tau_px),
+                                    alpha, counts.ctypes.data, ctypes.byref(best),
+                                    ctypes.byref(n_in)), "sr_fit_alpha")
+    return {"alpha": np.array(alpha[:]), "counts": counts, "best": best.value,
+            "n_inliers": n_in.value}
+
+
+def sr_fit_roll(ctx, d_disp, u_lo: int, v_lo: int, u_hi: int, v_hi: int):
+    """Plane d = g0 + g1 u + g2 v over a patch; returns (g[3], roll, n)."""
+    g = (ctypes.c_double * 3)()
+    roll, n = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(ctx, load().sr_fit_roll(ctx, _ptr(d_disp), int(u_lo), int(v_lo), int(u_hi), int(v_hi),
+                                   g, ctypes.byref(roll), ctypes.byref(n)), "sr_fit_roll")
+    return np.array(g[:]), roll.value, n.value
 
 
 def sr_get_buffer(ctx, which: int, dst, nbytes: int) -> int:
