@@ -665,6 +665,83 @@ def fit_report(steps: int, warmup: int):
     return out
 
 
+def accuracy_report(steps: int, warmup: int):
+    """Synthetic analogue of the Sec. III sample-model experiment: on the
+    1280x720 scene (f = 700 px, baseline 120 mm), for every pothole clear of
+    the other depressions and the frame border, fit the road plane to the
+    reconstructed 3-D points of a ring around it (4 to 6 sigma), then take
+    the distance to that plane of the reconstructed points near its bottom
+    (within sigma / 2) as the measured depth.  The same construction on the
+    generator's true disparity gives the true depth.  The error is measured
+    minus true depth, in mm."""
+    import numpy as np
+    import torch
+
+    from paper_1807_07433_gb300 import sr, synth
+    w = synth.C2
+    sc = w.scene
+    left, right, d_true = synth.make_pair(sc)
+    pots, grooves = synth.features(sc)
+    H, W = left.shape
+    f, B = w.f_px, w.baseline_mm
+    u0, v0 = (W - 1) / 2.0, (H - 1) / 2.0
+    dev = torch.device("cuda", 0)
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream(dev)) as m:
+        m.set_plane(sc.alpha0, sc.alpha1, w.delta)
+        m.set_camera(f, B, u0, v0)
+        disp = m.match(torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev))
+        xyz = m.reconstruct(disp).cpu().numpy().astype(np.float64)
+    vv, uu = np.mgrid[0:H, 0:W].astype(np.float64)
+    Zt = f * B / d_true
+    xyz_t = np.stack([(uu - u0) * Zt / f, (vv - v0) * Zt / f, Zt])
+
+    groove_mask = np.zeros((H, W), bool)
+    for pts, half_w, _ in grooves:
+        for (x0, y0), (x1, y1) in zip(pts[:-1], pts[1:]):
+            ex, ey = x1 - x0, y1 - y0
+            t = np.clip(((uu - x0) * ex + (vv - y0) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
+            groove_mask |= np.hypot(uu - (x0 + t * ex), vv - (y0 + t * ey)) < half_w + 3.0
+
+    def plane_dist(P, Q):
+        """distances of points Q (N x 3) to the least-squares plane of P (M x 3)"""
+        c = P.mean(0)
+        n = np.linalg.svd(P - c, full_matrices=False)[2][-1]
+        return np.abs((Q - c) @ n)
+
+    rows = []
+    for k, (uk, vk, a, s) in enumerate(pots):
+        if not (6 * s <= uk < W - 6 * s and 6 * s <= vk < H - 6 * s):
+            continue
+        if any(j != k and np.hypot(uk - uj, vk - vj) < 6 * s + 4 * sj
+               for j, (uj, vj, _, sj) in enumerate(pots)):
+            continue
+        r = np.hypot(uu - uk, vv - vk)
+        ring = (r >= 4 * s) & (r <= 6 * s) & ~groove_mask
+        core = (r <= 0.5 * s) & ~groove_mask
+        if groove_mask[(r <= 6 * s)].any() or (d_true[core] <= sc.alpha0 + sc.alpha1 * vv[core] - 2.0).any():
+            continue
+        ok_ring = ring & np.isfinite(xyz[2])
+        ok_core = core & np.isfinite(xyz[2])
+        if ok_ring.sum() < 50 or ok_core.sum() < 5:
+            continue
+        meas = plane_dist(xyz[:, ok_ring].T, xyz[:, ok_core].T)
+        true = plane_dist(xyz_t[:, ok_ring].T, xyz_t[:, ok_core].T)
+        err = meas - true
+        rows.append({"pothole": k, "u": round(uk, 1), "v": round(vk, 1), "depth_px": round(a, 3),
+                     "sigma_px": round(s, 2), "true_depth_mm": round(float(true.mean()), 2),
+                     "measured_depth_mm": round(float(meas.mean()), 2),
+                     "error_mm_mean": round(float(err.mean()), 3),
+                     "error_mm_rms": round(float(np.sqrt((err ** 2).mean())), 3),
+                     "points": int(ok_core.sum())})
+    allerr = np.array([r["error_mm_mean"] for r in rows])
+    return {"report": "accuracy", "workload": w.name, "f_px": f, "baseline_mm": B,
+            "potholes_used": len(rows), "potholes_in_scene": len(pots),
+            "mean_abs_error_mm": round(float(np.abs(allerr).mean()), 3) if len(rows) else None,
+            "max_abs_error_mm": round(float(np.abs(allerr).max()), 3) if len(rows) else None,
+            "paper_reported_accuracy_mm": 3.0, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,7 +749,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit"), default=None,
+    ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit", "accuracy"), default=None,
                     help="print a report instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -691,6 +768,9 @@ def main():
         return
     if args.report == "fit":
         print(json.dumps(fit_report(args.steps, args.warmup)), flush=True)
+        return
+    if args.report == "accuracy":
+        print(json.dumps(accuracy_report(args.steps, args.warmup)), flush=True)
         return
     from paper_1807_07433_gb300 import synth
     w = synth.C2

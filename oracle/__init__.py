@@ -87,6 +87,8 @@ def _load():
                 "orc_postprocess": (d, [pp, d, i]),
                 "orc_reconstruct": (None, [pp, d, i, i, vp, vp, vp]),
                 "orc_match": (i, [pp, vp, vp, i, i, ctypes.POINTER(_Outputs)]),
+                "orc_match_restricted": (i, [pp, vp, vp, vp, i, i, i, ctypes.POINTER(_Outputs)]),
+                "orc_wta_window": (i, [vp, i, i, vp]),
                 "orc_match_pixels": (i, [pp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp,
                                          vp, vp, vp]),
                 "orc_objective": (d, [pp, vp, vp, vp]),
@@ -243,9 +245,12 @@ _VOLUMES = ("cost_l", "cost_r", "agg_l", "agg_r")
 
 def match(p: Params, left: np.ndarray, right: np.ndarray, rows: tuple[int, int] | None = None,
           want: tuple[str, ...] = ("lbl_l", "lbl_r", "gap_l", "gap_r", "den_l", "dsub",
-                                   "valid", "dfull", "xyz")) -> MatchResult:
+                                   "valid", "dfull", "xyz"),
+          centre: np.ndarray | None = None, radius: int | None = None) -> MatchResult:
     """Run the whole pipeline (or a band of output rows) and return the
-    requested arrays.  Unrequested arrays are not computed or stored."""
+    requested arrays.  Unrequested arrays are not computed or stored.  With
+    centre ([H, W] residual disparities) and radius, every pixel searches only
+    [centre - radius, centre + radius] (clamped to 0..D-1)."""
     left, right = _u8(left), _u8(right)
     assert left.shape == (p.H, p.W) and right.shape == (p.H, p.W)
     H, W, D = p.H, p.W, p.D
@@ -270,11 +275,25 @@ def match(p: Params, left: np.ndarray, right: np.ndarray, rows: tuple[int, int] 
         setattr(res, name, arr)
         setattr(outs, name, arr.ctypes.data)
     r0, r1 = (0, H) if rows is None else rows
-    rc = _load().orc_match(ctypes.byref(p.c()), _ptr(left), _ptr(right), int(r0), int(r1),
-                           ctypes.byref(outs))
+    if centre is None:
+        rc = _load().orc_match(ctypes.byref(p.c()), _ptr(left), _ptr(right), int(r0), int(r1),
+                               ctypes.byref(outs))
+    else:
+        c = np.ascontiguousarray(centre, dtype=np.int32)
+        assert c.shape == (H, W) and radius is not None
+        rc = _load().orc_match_restricted(ctypes.byref(p.c()), _ptr(left), _ptr(right), _ptr(c),
+                                          int(radius), int(r0), int(r1), ctypes.byref(outs))
     if rc != 0:
         raise RuntimeError(f"orc_match failed with {rc}")
     return res
+
+
+def wta_window(c: np.ndarray, lo: int, hi: int):
+    """WTA over c[lo..hi] (ties: smallest d); returns (d, gap)."""
+    c = _f64(c)
+    gap = ctypes.c_double(0.0)
+    d = _load().orc_wta_window(_ptr(c), int(lo), int(hi), ctypes.byref(gap))
+    return d, gap.value
 
 
 def match_pixels(p: Params, left: np.ndarray, right: np.ndarray, us, vs) -> dict:

@@ -236,6 +236,42 @@ double orc_parabola(const double *c, int D, int d, double *den) {
     return (double)d + (cm - cp) / q;
 }
 
+/* Restricted search (the paper's Sec. IV plan: filter only the space around
+ * previously calculated disparities).  Pixel p searches the window
+ * [max(0, c - r), min(D - 1, c + r)] around its centre c (clamped to
+ * 0..D-1) instead of 0..D-1: WTA and Eq. 12 as above with the window's ends
+ * in the role of 0 and D - 1.  The aggregated costs are those of Eq. 8. */
+static void search_window(int D, int centre, int radius, int *lo, int *hi) {
+    const int c = clampi(centre, 0, D - 1);
+    *lo = c - radius < 0 ? 0 : c - radius;
+    *hi = c + radius > D - 1 ? D - 1 : c + radius;
+}
+
+int orc_wta_window(const double *c, int lo, int hi, double *gap) {
+    int best = lo;
+    for (int d = lo + 1; d <= hi; ++d)
+        if (c[d] > c[best]) best = d;
+    if (gap) {
+        double second = -INFINITY;
+        for (int d = lo; d <= hi; ++d)
+            if (d != best && c[d] > second) second = c[d];
+        *gap = (hi > lo) ? c[best] - second : INFINITY;
+    }
+    return best;
+}
+
+double orc_parabola_window(const double *c, int lo, int hi, int d, double *den) {
+    if (d <= lo || d >= hi) {
+        if (den) *den = 0.0;
+        return (double)d;
+    }
+    const double cm = c[d - 1], c0 = c[d], cp = c[d + 1];
+    const double q = 2.0 * cm + 2.0 * cp - 4.0 * c0;
+    if (den) *den = q;
+    if (!(q < 0.0)) return (double)d;
+    return (double)d + (cm - cp) / q;
+}
+
 /* Eq. 11 with a tolerance: pixel u of a row passes iff its match u - l_ref
  * lies in the image and the target map agrees there within lr_thresh. */
 int orc_lr_valid(int u, int lref, const int32_t *ltar_row, double lr_thresh) {
@@ -284,10 +320,13 @@ static void cost_rows(const orc_params *p, const double *L, const double *R, int
     }
 }
 
-/* Full pipeline (Fig. 1 order) for output rows [row_begin, row_end).
+/* Full pipeline (Fig. 1 order) for output rows [row_begin, row_end); with
+ * centre != NULL, every pixel of both views searches only its window around
+ * centre[v*W+u] (see search_window).
  * Returns 0 on success, -1 on bad arguments, -2 on allocation failure. */
-int orc_match(const orc_params *p, const uint8_t *il, const uint8_t *ir,
-              int row_begin, int row_end, orc_outputs *out) {
+static int match_impl(const orc_params *p, const uint8_t *il, const uint8_t *ir,
+                      const int32_t *centre, int radius, int row_begin, int row_end,
+                      orc_outputs *out) {
     const int W = p->W, H = p->H, D = p->D, rho = p->agg_r;
     if (W < 1 || H < 1 || D < 1 || p->ncc_r < 0 || rho < 0) return -1;
     if (row_begin < 0) row_begin = 0;
@@ -364,13 +403,15 @@ int orc_match(const orc_params *p, const uint8_t *il, const uint8_t *ir,
                     bilateral_all_d(vr, D, R, W, H, rho, p->gamma_d, p->gamma_r, u, v, num, ar);
                     if (out->agg_l) memcpy(out->agg_l + i * D, al, (size_t)D * sizeof(double));
                     if (out->agg_r) memcpy(out->agg_r + i * D, ar, (size_t)D * sizeof(double));
+                    int lo = 0, hi = D - 1;
+                    if (centre) search_window(D, centre[i], radius, &lo, &hi);
                     double g;
-                    lbl_l[i] = orc_wta(al, D, &g);
+                    lbl_l[i] = orc_wta_window(al, lo, hi, &g);
                     if (out->gap_l) out->gap_l[i] = g;
-                    lbl_r[i] = orc_wta(ar, D, &g);
+                    lbl_r[i] = orc_wta_window(ar, lo, hi, &g);
                     if (out->gap_r) out->gap_r[i] = g;
                     double q;
-                    dsub[i] = orc_parabola(al, D, lbl_l[i], &q);
+                    dsub[i] = orc_parabola_window(al, lo, hi, lbl_l[i], &q);
                     if (out->den_l) out->den_l[i] = q;
                 }
             }
@@ -398,6 +439,18 @@ int orc_match(const orc_params *p, const uint8_t *il, const uint8_t *ir,
     if (base != 0) { free(cl); free(cr); }
     free(L); free(R);
     return err ? -2 : 0;
+}
+
+int orc_match(const orc_params *p, const uint8_t *il, const uint8_t *ir,
+              int row_begin, int row_end, orc_outputs *out) {
+    return match_impl(p, il, ir, NULL, 0, row_begin, row_end, out);
+}
+
+int orc_match_restricted(const orc_params *p, const uint8_t *il, const uint8_t *ir,
+                         const int32_t *centre, int radius, int row_begin, int row_end,
+                         orc_outputs *out) {
+    if (!centre || radius < 0) return -1;
+    return match_impl(p, il, ir, centre, radius, row_begin, row_end, out);
 }
 
 /* Aggregated cost vector at one pixel, every NCC value evaluated on demand

@@ -147,6 +147,15 @@ def _depth(u: np.ndarray, v: np.ndarray, pots, grooves) -> np.ndarray:
     return np.minimum(dep, 2.0)
 
 
+def features(sc: Scene):
+    """The scene's potholes [(u, v, depth_px, sigma_px)] and grooves, drawn in
+    the order make_pair draws them (same generator state)."""
+    rng = np.random.Generator(np.random.PCG64(sc.seed))
+    d_hi = sc.alpha0 + sc.alpha1 * sc.H + 4.0
+    _lattice_noise(rng, sc.W + d_hi + 8.0, sc.H + 2.0)
+    return _depressions(rng, sc)
+
+
 def make_pair(sc: Scene):
     """Render (left uint8 [H,W], right uint8 [H,W], true disparity float64 [H,W])."""
     rng = np.random.Generator(np.random.PCG64(sc.seed))
