@@ -742,6 +742,80 @@ def accuracy_report(steps: int, warmup: int):
             "paper_reported_accuracy_mm": 3.0, "rows": rows}
 
 
+def restricted_report(steps: int, warmup: int):
+    """Restricted search (the paper's Sec. IV plan) on the benchmark frame:
+    sr_match against sr_match_restricted with (a) the plane hypothesis (every
+    pixel centred at round(delta)) and (b) the previous frame's labels (the
+    full search's WTA map) as centres; device time per frame (median, CUDA
+    events, L2 flushed), label agreement with the full search, and the FP64
+    oracle's restricted search on the full frame for (a)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1807_07433_gb300 import sr, synth
+    w = synth.C2
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    dl, dr = torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {"report": "restricted", "workload": w.name, "steps": steps, "warmup": warmup}
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=stream) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        wta_full = torch.empty((H, W), dtype=torch.int16, device=dev)
+
+        def timed(fn):
+            for _ in range(warmup):
+                fn()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return r, statistics.median(ms)
+        d_full, t_full = timed(lambda: m.match(dl, dr, wta=wta_full))
+        d_full = d_full.cpu().numpy()
+        lbl_full = wta_full.cpu().numpy()
+        out["full"] = {"ms": round(t_full, 4), "mdes": round(mdes(W, H, w.D, t_full * 1e-3), 1),
+                       "valid_fraction": round(float(np.isfinite(d_full).mean()), 4)}
+        forms = {"plane_r4": (None, 4), "previous_labels_r3": (wta_full.clone(), 3),
+                 "previous_labels_r2": (wta_full.clone(), 2)}
+        for name, (centre, r) in forms.items():
+            wta = torch.empty((H, W), dtype=torch.int16, device=dev)
+            d, t = timed(lambda: m.match_restricted(dl, dr, r, centre=centre, wta=wta))
+            d = d.cpu().numpy()
+            lbl = wta.cpu().numpy()
+            both = np.isfinite(d) & np.isfinite(d_full)
+            out[name] = {"ms": round(t, 4),
+                         "mdes_equivalent": round(mdes(W, H, w.D, t * 1e-3), 1),
+                         "speedup_vs_full": round(t_full / t, 3),
+                         "label_agreement_with_full": round(float((lbl == lbl_full).mean()), 5),
+                         "valid_fraction": round(float(np.isfinite(d).mean()), 4),
+                         "dfull_max_abs_diff_where_both_valid_px":
+                             float(np.abs(d[both] - d_full[both]).max())}
+            if name == "plane_r4":
+                p = oracle.Params(W=W, H=H, D=w.D, ncc_r=w.ncc_r, agg_r=w.agg_r,
+                                  gamma_d=w.gamma_d, gamma_r=w.gamma_r, lr_thresh=w.lr_thresh,
+                                  alpha0=w.scene.alpha0, alpha1=w.scene.alpha1, delta=w.delta)
+                t0 = time.perf_counter()
+                o = oracle.match(p, left, right, want=("lbl_l", "gap_l"),
+                                 centre=np.full((H, W), int(round(w.delta))), radius=r)
+                diff = lbl != o.lbl_l
+                out[name]["oracle"] = {
+                    "label_mismatch_pct": round(100.0 * diff.mean(), 4),
+                    "label_mismatch_outside_gap_1e-4_pct":
+                        round(100.0 * (diff & (o.gap_l >= 1e-4)).mean(), 4),
+                    "oracle_s": round(time.perf_counter() - t0, 2)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -749,7 +823,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit", "accuracy"), default=None,
+    ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit", "accuracy",
+                                                "restricted"), default=None,
                     help="print a report instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -771,6 +846,9 @@ def main():
         return
     if args.report == "accuracy":
         print(json.dumps(accuracy_report(args.steps, args.warmup)), flush=True)
+        return
+    if args.report == "restricted":
+        print(json.dumps(restricted_report(args.steps, args.warmup)), flush=True)
         return
     from paper_1807_07433_gb300 import synth
     w = synth.C2

@@ -120,6 +120,26 @@ sr_status sr_set_camera(sr_ctx *ctx, double f_px, double baseline, double u0, do
 sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                    float *d_disp, int16_t *d_wta_or_null);
 
+/* Restricted search: sr_match with every pixel of both views searching only
+ * the window [c - radius, c + radius] (clamped to 0..D-1) around its centre
+ * c, the plan of the paper's Sec. IV (filter only the space around previously
+ * calculated disparities).  WTA (Sec. II-B-3) and Eq. 12 run over the window,
+ * with its ends in the role of 0 and D-1 (no parabola at an end); the
+ * aggregated costs themselves are those of sr_match, which this call equals
+ * when radius >= D-1.
+ *   d_centre   W x H int16 residual disparities (e.g. the WTA map of the
+ *              previous frame, d_wta_or_null of sr_match), or NULL for the
+ *              plane hypothesis: every pixel centred at round(delta)
+ *   radius     0 <= radius < D
+ * The aggregation runs only where needed: each 32 x 4 tile whose windows fit
+ * one 16-disparity slice aggregates just that slice (read through a TMA
+ * tensor map), the others aggregate all D.  The NCC volumes are computed in
+ * full.  Asynchronous; the first call allocates one int per tile and builds
+ * the tensor maps.  Errors: SR_ERR_INVALID_ARG, SR_ERR_CUDA. */
+sr_status sr_match_restricted(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
+                              int pitch_bytes, const int16_t *d_centre, int radius,
+                              float *d_disp, int16_t *d_wta_or_null);
+
 /* sr_match with host buffers: copies h_left/h_right (W x H, dense) to the
  * device, runs sr_match, copies the disparity map back into h_disp (W x H
  * float) and synchronises the stream.  Pinned host memory makes the copies
@@ -306,6 +326,7 @@ sr_status sr_get_buffer(sr_ctx *ctx, sr_buffer which, void *dst, size_t *bytes_i
  * stays usable. */
 #define SR_DEBUG_KEEP_AGG 1
 #define SR_DEBUG_WITHHOLD_ROW 2
+#define SR_DEBUG_NO_BAND 4       /* sr_match_restricted: every tile runs the full-D kernel */
 sr_status sr_set_debug(sr_ctx *ctx, int flags);
 
 /* Wait for the context's queued work.  Device-side waits are bounded; when

@@ -35,6 +35,8 @@
 //     changes neither the argmax nor the parabola vertex, so it is applied
 //     only when the aggregated volume is exported.
 #pragma once
+#include <cuda.h>
+
 #include "sr_internal.cuh"
 
 namespace sr {
@@ -51,11 +53,14 @@ struct AggCfg {
     static constexpr int WS = 2 * R + 1;           // window side
     static constexpr int TXE = kAggTX + 2 * R;     // ring row width (pixels)
     static constexpr int TYE = kAggTY + 2 * R;     // source rows per tile
-    static constexpr int RING = TXE * D;           // elements per cost-ring slot
+    static constexpr int RING = TXE * D;           // elements of one cost row of the tile
+    // slot stride: RING rounded up to 128 bytes, the alignment a tensor-map
+    // copy needs for its destination
+    static constexpr int RINGS = (int)(((RING * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
     static constexpr int WRING = kAggTY * WS * kAggTX;  // floats per weight slot
     // shared memory, in bytes: [cost ring | weight ring] (reused by the
     // epilogue transpose), guide tile, weight sums, two mbarriers
-    static constexpr size_t RINGB = 2 * (size_t)RING * sizeof(VT);
+    static constexpr size_t RINGB = 2 * (size_t)RINGS * sizeof(VT);
     static constexpr size_t RINGSB = RINGB + 2 * (size_t)WRING * sizeof(float);
     static constexpr size_t EPIB = (size_t)kAggPix * (D + 1) * sizeof(float);
     static constexpr size_t UNIONB = ((RINGSB > EPIB ? RINGSB : EPIB) + 15) / 16 * 16;
@@ -91,6 +96,18 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Two-dimensional TMA tile copy global -> shared through a tensor map,
+// completing on an mbarrier: box origin (x, y) in elements (x the inner
+// coordinate, 16-byte aligned; y may be negative or past the end, where the
+// box reads zeros).
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x), "r"(y), "r"(smem_addr(bar))
         : "memory");
 }
 // Wait for the phase of the given parity; gives up after max_cycles SM clocks
@@ -149,14 +166,21 @@ __device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT> &sm) {
 // One 32 x 4 tile at (x0, y0) with all D disparities.  ph holds, per ring
 // slot, the parity of the slot's next mbarrier phase; it carries over from
 // tile to tile of a persistent CTA.  All threads of the CTA take part.
-template <int R, int D, bool GU8, typename VT>
+//
+// BAND: the ring holds the D = kBandD disparities [dlo, dlo + D) of each pixel,
+// loaded as one 2-D tensor-map box per row (tmap); otherwise the D
+// disparities of the volume, one bulk copy per row.  win restricts the WTA
+// and Eq. 12 of each pixel to its window (see AggWin).
+template <int R, int D, bool GU8, typename VT, bool BAND = false>
 __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &ph,
                                          const VT *__restrict__ vol, const uint8_t *__restrict__ gl,
                                          int pitch, const float *__restrict__ gf, int W, int H,
                                          float kd, float kr, int16_t *__restrict__ lbl,
                                          float *__restrict__ dsub, float *__restrict__ agg,
                                          int *__restrict__ err, long long wait_cycles,
-                                         int withhold_last, int x0, int y0) {
+                                         int withhold_last, int x0, int y0,
+                                         const void *tmap = nullptr, int dlo = 0,
+                                         const AggWin &win = AggWin()) {
     using C = AggCfg<R, D, VT>;
     float *smem = sm.epi();                      // epilogue view
     VT *ring = sm.ring();                        // [2][TXE][D] cost rows
@@ -181,7 +205,14 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
             mbar_arrive(bar);   // no copy: complete the phase to keep the slot in step
             return;
         }
-        VT *dst = ring + (j & 1) * C::RING + (xs - (x0 - R)) * D;
+        if (BAND) {
+            // the whole box: pixels beyond the row's ends come from the
+            // neighbouring rows (or are zeros) and meet zero weights
+            mbar_arrive_expect_tx(bar, (unsigned)(C::RING * sizeof(VT)));
+            tma_load_2d(ring + (j & 1) * C::RINGS, tmap, dlo, y * W + x0 - R, bar);
+            return;
+        }
+        VT *dst = ring + (j & 1) * C::RINGS + (xs - (x0 - R)) * D;
         const VT *src = vol + ((size_t)y * W + xs) * D;
         mbar_arrive_expect_tx(bar, row_bytes);
         tma_load_1d(dst, src, row_bytes, bar);
@@ -233,9 +264,9 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
             g = GU8 ? (float)gl[(size_t)y * pitch + x] : gf[(size_t)y * W + x];
         guide[i] = g;
     }
-    if (xs > x0 - R || xe < x0 + kAggTX + R) {
-        for (int i = tid; i < 2 * C::RING; i += C::NT) {
-            const int c = (i % C::RING) / D + x0 - R;
+    if (!BAND && (xs > x0 - R || xe < x0 + kAggTX + R)) {
+        for (int i = tid; i < 2 * C::RINGS; i += C::NT) {
+            const int c = (i % C::RINGS) / D + x0 - R;
             if (c < xs || c >= xe) ring[i] = VT(0.0f);
         }
     }
@@ -271,7 +302,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         const int y = y0 - R + j;
         if (y >= 0 && y < H) {
             mbar_wait(bars + (j & 1), (ph >> (j & 1)) & 1u, wait_cycles, err);
-            const VT *rs = ring + (j & 1) * C::RING + bx * D + 2 * sl;
+            const VT *rs = ring + (j & 1) * C::RINGS + bx * D + 2 * sl;
             const float *ws = wring + (j & 1) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
 #pragma unroll
@@ -322,18 +353,34 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         const int u = x0 + tpx, v = y0 + py;
         if (u >= W || v >= H) continue;
         const float *e = E + pw * (D + 1);
-        int best = 0;
-        float cb = e[0];
-#pragma unroll 8
-        for (int d = 1; d < D; ++d) {
-            const float c = e[d];
-            if (c > cb) { cb = c; best = d; }
-        }
         const size_t o = (size_t)v * W + u;
-        lbl[o] = (int16_t)best;
+        // search window in slice indices: 0..D-1, or the pixel's window
+        int lo = 0, hi = D - 1;
+        if (win.radius >= 0) {
+            int cc = win.centre ? win.centre[o] : win.centre_const;
+            cc = min(max(cc, 0), win.dfull - 1);
+            lo = max(max(cc - win.radius, 0) - dlo, 0);         // the clamps only
+            hi = min(min(cc + win.radius, win.dfull - 1) - dlo, D - 1);   // keep bad input in bounds
+            if (hi < lo) hi = lo;
+        }
+        int best = lo;
+        float cb = e[lo];
+        if (lo == 0 && hi == D - 1) {
+#pragma unroll 8
+            for (int d = 1; d < D; ++d) {
+                const float c = e[d];
+                if (c > cb) { cb = c; best = d; }
+            }
+        } else {
+            for (int d = lo + 1; d <= hi; ++d) {
+                const float c = e[d];
+                if (c > cb) { cb = c; best = d; }
+            }
+        }
+        lbl[o] = (int16_t)(best + dlo);
         if (dsub) {
-            float ds = (float)best;
-            if (best > 0 && best < D - 1) {
+            float ds = (float)(best + dlo);
+            if (best > lo && best < hi) {
                 const float cm = e[best - 1], cp = e[best + 1];
                 const float den = 2.0f * cm + 2.0f * cp - 4.0f * cb;
                 if (den < 0.0f) ds += (cm - cp) / den;
@@ -359,13 +406,35 @@ __global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
 k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
           const float *__restrict__ gf, int W, int H, float kd, float kr,
           int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
-          int *__restrict__ err, long long wait_cycles, int withhold_last) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+          int *__restrict__ err, long long wait_cycles, int withhold_last, AggWin win) {
+    // restricted search: tiles of the band kernel are not this kernel's
+    if (win.band && win.band[blockIdx.y * gridDim.x + blockIdx.x] >= 0) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const AggSmem<R, D, VT> sm{smem_raw};
     agg_init_barriers(sm);
     unsigned ph = 0;
     agg_tile<R, D, GU8, VT>(sm, ph, vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, err,
-                            wait_cycles, withhold_last, blockIdx.x * kAggTX, blockIdx.y * kAggTY);
+                            wait_cycles, withhold_last, blockIdx.x * kAggTX, blockIdx.y * kAggTY,
+                            nullptr, 0, win);
+}
+
+// Band kernel of the restricted search: the tile's kBandD-disparity slice
+// [band, band + kBandD) through a 2-D tensor map of the volume.
+template <int R, bool GU8, typename VT>
+__global__ void __launch_bounds__(AggCfg<R, kBandD, VT>::NT, AggCfg<R, kBandD, VT>::MINB)
+k_agg_band(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ gl, int pitch,
+           const float *__restrict__ gf, int W, int H, float kd, float kr,
+           int16_t *__restrict__ lbl, float *__restrict__ dsub, int *__restrict__ err,
+           long long wait_cycles, AggWin win) {
+    const int dlo = win.band[blockIdx.y * gridDim.x + blockIdx.x];
+    if (dlo < 0) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const AggSmem<R, kBandD, VT> sm{smem_raw};
+    agg_init_barriers(sm);
+    unsigned ph = 0;
+    agg_tile<R, kBandD, GU8, VT, true>(sm, ph, nullptr, gl, pitch, gf, W, H, kd, kr, lbl, dsub,
+                                       nullptr, err, wait_cycles, 0, blockIdx.x * kAggTX,
+                                       blockIdx.y * kAggTY, &tmap, dlo, win);
 }
 
 // Persistent batched form: CTA b handles work items b, b + gridDim.x, ... of
@@ -375,7 +444,7 @@ template <int R, int D, bool TARGET, typename VT>
 __global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
 k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, int n, float kd,
             float kr, int *__restrict__ err, long long wait_cycles, int *__restrict__ next) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const AggSmem<R, D, VT> sm{smem_raw};
     agg_init_barriers(sm);
     // The loop state lives in shared memory and is re-read after each tile,
@@ -413,14 +482,29 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
 template <int R, int D, typename VT>
 cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
-                         const AggDebug &dbg, cudaStream_t st) {
+                         const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
     using C = AggCfg<R, D, VT>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
     auto k = gl ? k_agg_wta<R, D, true, VT> : k_agg_wta<R, D, false, VT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
-                                    dbg.wait_cycles, dbg.withhold_last);
+                                    dbg.wait_cycles, dbg.withhold_last, win);
+    return cudaGetLastError();
+}
+
+template <int R, typename VT>
+cudaError_t agg_band_launch_t(const CUtensorMap &tmap, const uint8_t *gl, int pitch,
+                              const float *gf, int W, int H, float kd, float kr, int16_t *lbl,
+                              float *dsub, const AggDebug &dbg, const AggWin &win,
+                              cudaStream_t st) {
+    using C = AggCfg<R, kBandD, VT>;
+    const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
+    auto k = gl ? k_agg_band<R, true, VT> : k_agg_band<R, false, VT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    k<<<grid, C::NT, C::SMEM, st>>>(tmap, gl, pitch, gf, W, H, kd, kr, lbl, dsub, dbg.err,
+                                    dbg.wait_cycles, win);
     return cudaGetLastError();
 }
 
@@ -460,9 +544,19 @@ int agg_occ_t() {
 template <int D, typename VT>
 cudaError_t agg_launch_d(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub,
-                         float *agg, const AggDebug &dbg, cudaStream_t st) {
+                         float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
     SR_AGG_R_SWITCH(agg_r, return (agg_launch_t<R_, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl,
-                                                           dsub, agg, dbg, st)))
+                                                           dsub, agg, dbg, st, win)))
+    return cudaErrorInvalidValue;
+}
+
+template <typename VT>
+cudaError_t agg_band_launch_d(const CUtensorMap &tmap, const uint8_t *gl, int pitch,
+                              const float *gf, int W, int H, int agg_r, float kd, float kr,
+                              int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win,
+                              cudaStream_t st) {
+    SR_AGG_R_SWITCH(agg_r, return (agg_band_launch_t<R_, VT>(tmap, gl, pitch, gf, W, H, kd, kr,
+                                                             lbl, dsub, dbg, win, st)))
     return cudaErrorInvalidValue;
 }
 

@@ -14,23 +14,27 @@
 
 namespace sr {
 cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d16_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d16_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d32_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d64_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
-cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+
+cudaError_t launch_agg_band_f32(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
+cudaError_t launch_agg_band_f16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
+cudaError_t launch_agg_band_bf16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 
 cudaError_t launch_ncc_batch_d16_f32(bool, const PairDesc *, const int *, int, int, int, int *, cudaStream_t);
 cudaError_t launch_agg_batch_d16_f32(bool, const PairDesc *, const int *, int, int, float, float, const AggDebug &, int, int *, cudaStream_t);
@@ -99,13 +103,27 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
 cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
-                       const AggDebug &dbg, cudaStream_t st) {
+                       const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
     const float log2e = 1.4426950408889634f;
     const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
     switch (D) {
-        case 16: SR_VT_DISPATCH(launch_agg, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st)
-        case 32: SR_VT_DISPATCH(launch_agg, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st)
-        case 64: SR_VT_DISPATCH(launch_agg, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st)
+        case 16: SR_VT_DISPATCH(launch_agg, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+        case 32: SR_VT_DISPATCH(launch_agg, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+        case 64: SR_VT_DISPATCH(launch_agg, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_agg_band(const void *tmap, int vt, const uint8_t *guide_u8, int pitch,
+                            const float *guide_f32, int W, int H, int agg_r, float gamma_d,
+                            float gamma_r, int16_t *lbl, float *dsub, const AggDebug &dbg,
+                            const AggWin &win, cudaStream_t st) {
+    const float log2e = 1.4426950408889634f;
+    const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
+    switch (vt) {
+        case kVolF32: return launch_agg_band_f32(tmap, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, dbg, win, st);
+        case kVolF16: return launch_agg_band_f16(tmap, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, dbg, win, st);
+        case kVolBF16: return launch_agg_band_bf16(tmap, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, dbg, win, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -179,7 +197,7 @@ void free_all(sr_ctx *c) {
     void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
                     c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
                     c->stage_disp, c->d_err, c->g_vol, c->g_wsum, c->g_rw, c->g_partial,
-                    c->f_pairs, c->f_has, c->f_counts, c->f_model, c->f_partial};
+                    c->f_pairs, c->f_has, c->f_counts, c->f_model, c->f_partial, c->band};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)
@@ -188,6 +206,43 @@ void free_all(sr_ctx *c) {
 }
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a cost volume [H][W][D] viewed as [H*W][D], box kBandD
+// disparities x (32 + 2 agg_r) pixels, zeros outside.
+bool encode_volume_map(CUtensorMap *m, void *vol, int vt, int W, int H, int D, int agg_r) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = vt == sr::kVolF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : vt == sr::kVolF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)W * H};
+    const cuuint64_t strides[1] = {(cuuint64_t)D * sr::vol_elem_bytes(vt)};
+    const cuuint32_t box[2] = {(cuuint32_t)sr::kBandD, (cuuint32_t)(32 + 2 * agg_r)};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, dt, 2, vol, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // IEEE 754 binary16 bit pattern -> float (sign, 5-bit exponent, 10-bit fraction).
 float half_bits_to_float(uint16_t h) {
@@ -309,7 +364,8 @@ sr_status sr_set_camera(sr_ctx *c, double f_px, double baseline, double u0, doub
 }
 
 sr_status sr_set_debug(sr_ctx *c, int flags) {
-    if (!c || (flags & ~(SR_DEBUG_KEEP_AGG | SR_DEBUG_WITHHOLD_ROW))) return SR_ERR_INVALID_ARG;
+    if (!c || (flags & ~(SR_DEBUG_KEEP_AGG | SR_DEBUG_WITHHOLD_ROW | SR_DEBUG_NO_BAND)))
+        return SR_ERR_INVALID_ARG;
     if ((flags & SR_DEBUG_KEEP_AGG) && !c->agg_l) {
         const size_t n = (size_t)c->p.width * c->p.height * c->p.max_disp;
         SR_TRY(c, dalloc(&c->agg_l, n), "cudaMalloc(agg_l)");
@@ -389,6 +445,76 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     c->matched = true;
     c->agg_valid = keep;
     c->timed = prof;
+    return SR_OK;
+}
+
+sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right,
+                              int pitch_bytes, const int16_t *d_centre, int radius, float *d_disp,
+                              int16_t *d_wta_or_null) {
+    if (!c || !d_left || !d_right || !d_disp || pitch_bytes < c->p.width) return SR_ERR_INVALID_ARG;
+    const sr_params &p = c->p;
+    const int W = p.width, H = p.height, D = p.max_disp;
+    if (radius < 0 || radius >= D) return SR_ERR_INVALID_ARG;
+    cudaStream_t st = c->st;
+    sr::AggWin win;
+    win.centre = d_centre;
+    win.centre_const = (int)lround(c->delta);
+    win.radius = radius;
+    win.dfull = D;
+    const bool banded = D > sr::kBandD && !(c->debug & SR_DEBUG_NO_BAND);
+    if (banded) {
+        if (!c->tmaps) {
+            if (!encode_volume_map(&c->tmap_l, c->vol_l, p.vol_dtype, W, H, D, p.agg_radius) ||
+                !encode_volume_map(&c->tmap_r, c->vol_r, p.vol_dtype, W, H, D, p.agg_radius)) {
+                snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed or is unavailable");
+                return SR_ERR_CUDA;
+            }
+            c->tmaps = true;
+        }
+        if (!c->band) {
+            const size_t tiles = (size_t)sr::ceil_div(W, sr::kAggTileX) * sr::ceil_div(H, sr::kAggTileY);
+            SR_TRY(c, dalloc(&c->band, tiles), "cudaMalloc(bands)");
+        }
+        win.band = c->band;
+        const int align = (int)(16 / sr::vol_elem_bytes(p.vol_dtype));
+        SR_TRY(c, sr::launch_tile_bands(win, W, H, align, c->band, st), "tile bands");
+    }
+    c->matched = false;
+    c->timed = false;
+    const sr::AggDebug dbg = agg_debug(c);
+    SR_TRY(c, sr::launch_warp(d_right, pitch_bytes, W, H, c->alpha0, c->alpha1, c->delta, c->rw, st),
+           "warp");
+    SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
+                               c->mu_r, c->inv_r, st),
+           "stats");
+    SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st),
+           "ncc_ref");
+    SR_TRY(c, sr::launch_ncc(true, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, p.vol_dtype, st),
+           "ncc_tgt");
+    if (banded) {
+        SR_TRY(c, sr::launch_agg_band(&c->tmap_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H,
+                                      p.agg_radius, p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, dbg,
+                                      win, st),
+               "agg_ref band");
+        SR_TRY(c, sr::launch_agg_band(&c->tmap_r, p.vol_dtype, nullptr, 0, c->rw, W, H,
+                                      p.agg_radius, p.gamma_d, p.gamma_r, c->lbl_r, nullptr, dbg,
+                                      win, st),
+               "agg_tgt band");
+    }
+    SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D,
+                             p.agg_radius, p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, nullptr, dbg,
+                             st, win),
+           "agg_ref");
+    SR_TRY(c, sr::launch_agg(c->vol_r, p.vol_dtype, nullptr, 0, c->rw, W, H, D, p.agg_radius,
+                             p.gamma_d, p.gamma_r, c->lbl_r, nullptr, nullptr, dbg, st, win),
+           "agg_tgt");
+    SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->alpha0, c->alpha1,
+                                  c->delta, p.lr_thresh, d_disp, d_wta_or_null, st),
+           "lrc_post");
+    c->matched = true;
+    c->agg_valid = false;
     return SR_OK;
 }
 

@@ -1,6 +1,7 @@
 // sr_ctx.cuh -- the context behind the opaque sr_ctx of include/sr.h, and the
 // error helpers shared by the ABI translation units.  Not installed.
 #pragma once
+#include <cuda.h>
 #include <stdio.h>
 
 #include "../../include/sr.h"
@@ -37,6 +38,10 @@ struct sr_ctx {
     // for 16-bit cost volumes, an FP32 reference volume [H*W*D]
     float *g_vol = nullptr, *g_wsum = nullptr, *g_rw = nullptr;
     double *g_partial = nullptr;     // block partials, then 3 results at the end
+    // sr_match_restricted: per-tile bands and tensor maps of the two volumes
+    int *band = nullptr;
+    bool tmaps = false;
+    CUtensorMap tmap_l{}, tmap_r{};
     // sr_fit_alpha / sr_fit_roll scratch, grown on demand
     int fit_cap = 0;                 // hypotheses the buffers hold
     int *f_pairs = nullptr, *f_has = nullptr, *f_counts = nullptr;

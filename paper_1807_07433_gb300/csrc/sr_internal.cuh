@@ -84,6 +84,22 @@ struct AggDebug {
     int withhold_last = 0;
 };
 
+// Restricted search (the paper's Sec. IV plan): pixel p searches only
+// [max(0, c - radius), min(dfull - 1, c + radius)] around its centre c
+// (centre[v*W+u], or centre_const when centre is null), clamped to 0..dfull-1.
+// radius < 0: the full search 0..D-1.  band (nullable): per 32 x 4 tile, the
+// first disparity of the band kernel's 16-wide slice (-1: the tile needs the
+// full-D kernel); the full-D kernel skips tiles with band >= 0.
+struct AggWin {
+    const int16_t *centre = nullptr;
+    int centre_const = 0;
+    int radius = -1;
+    int dfull = 0;
+    const int *band = nullptr;
+};
+constexpr int kBandD = 16;        // disparities per band-kernel slice
+constexpr int kAggTileX = 32, kAggTileY = 4;   // aggregation tile (pixels)
+
 // Eqs. 8-10 bilateral aggregation fused with WTA (Sec. II-B-3) and, for the
 // reference view, the Eq. 12 parabola.  Guide: the left image (uint8, when
 // guide_u8 != nullptr) or the warped target (float).  Writes lbl [H][W]
@@ -92,7 +108,21 @@ struct AggDebug {
 cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
-                       const AggDebug &dbg, cudaStream_t st);
+                       const AggDebug &dbg, cudaStream_t st, const AggWin &win = AggWin());
+
+// The band kernel of the restricted search: tiles with band >= 0 aggregate
+// the kBandD disparities [band, band + kBandD) of their pixels, read through
+// the 2-D tensor map tmap (a CUtensorMap over the volume viewed as
+// [H*W][D], box kBandD x (32 + 2 agg_r)); other tiles return at once.
+cudaError_t launch_agg_band(const void *tmap, int vt, const uint8_t *guide_u8, int pitch,
+                            const float *guide_f32, int W, int H, int agg_r, float gamma_d,
+                            float gamma_r, int16_t *lbl, float *dsub, const AggDebug &dbg,
+                            const AggWin &win, cudaStream_t st);
+// Per-tile bands of the restricted search (32 x 4 tiles, see AggWin):
+// band[t] = the aligned start of a kBandD slice holding every window of the
+// tile (align: 16 bytes of the stored type), or -1.
+cudaError_t launch_tile_bands(const AggWin &win, int W, int H, int align, int *band,
+                              cudaStream_t st);
 
 // Eq. 11 check with tolerance, then Sec. II-C post-processing.
 cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,

@@ -23,9 +23,11 @@ SR_VOL_F32, SR_VOL_F16, SR_VOL_BF16 = range(3)
  SR_BUF_COST_R, SR_BUF_AGG_L, SR_BUF_AGG_R, SR_BUF_WTA_L, SR_BUF_WTA_R, SR_BUF_DSUB) = range(12)
 SR_DEBUG_KEEP_AGG = 1
 SR_DEBUG_WITHHOLD_ROW = 2
+SR_DEBUG_NO_BAND = 4
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
+           "sr_match_restricted",
            "sr_match_host", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
            "sr_fit_alpha", "sr_fit_roll",
@@ -81,6 +83,7 @@ def load(path: str | None = None):
                 "sr_set_camera": (i, [vp, d, d, d, d]),
                 "sr_match": (i, [vp, vp, vp, i, vp, vp]),
                 "sr_match_host": (i, [vp, vp, vp, vp]),
+                "sr_match_restricted": (i, [vp, vp, vp, i, vp, i, vp, vp]),
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
                 "sr_match_batch": (i, [vp, i, ctypes.POINTER(sr_pair_desc)]),
@@ -172,6 +175,13 @@ def sr_set_camera(ctx, f_px: float, baseline: float, u0: float, v0: float) -> No
 def sr_match(ctx, d_left, d_right, pitch_bytes: int, d_disp, d_wta_or_null=None) -> None:
     _check(ctx, load().sr_match(ctx, _ptr(d_left), _ptr(d_right), int(pitch_bytes),
                                 _ptr(d_disp), _ptr(d_wta_or_null)), "sr_match")
+
+
+def sr_match_restricted(ctx, d_left, d_right, pitch_bytes: int, d_centre, radius: int, d_disp,
+                        d_wta_or_null=None) -> None:
+    _check(ctx, load().sr_match_restricted(ctx, _ptr(d_left), _ptr(d_right), int(pitch_bytes),
+                                           _ptr(d_centre), int(radius), _ptr(d_disp),
+                                           _ptr(d_wta_or_null)), "sr_match_restricted")
 
 
 def sr_match_host(ctx, h_left, h_right, h_disp) -> None:
@@ -355,6 +365,19 @@ class Matcher:
         pitch = left.stride(0) * left.element_size()
         assert right.stride(0) == left.stride(0), "left and right must share a pitch"
         sr_match(self.ctx, left, right, pitch, disp, wta)
+        return disp
+
+    def match_restricted(self, left, right, radius, centre=None, disp=None, wta=None):
+        """sr_match_restricted: search [centre - radius, centre + radius] per
+        pixel (centre: int16 [H, W] CUDA tensor, None = round(delta))."""
+        import torch
+        if disp is None:
+            disp = torch.empty((self.H, self.W), dtype=torch.float32, device=left.device)
+        pitch = left.stride(0) * left.element_size()
+        assert right.stride(0) == left.stride(0), "left and right must share a pitch"
+        if centre is not None:
+            assert centre.dtype == torch.int16 and centre.is_contiguous()
+        sr_match_restricted(self.ctx, left, right, pitch, centre, radius, disp, wta)
         return disp
 
     def reconstruct(self, disp, xyz=None):
