@@ -133,9 +133,11 @@ sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, i
  *   radius     0 <= radius < D
  * The aggregation runs only where needed: each 32 x 4 tile whose windows fit
  * one 16-disparity slice aggregates just that slice (read through a TMA
- * tensor map), the others aggregate all D.  The NCC volumes are computed in
- * full.  Asynchronous; the first call allocates one int per tile and builds
- * the tensor maps.  Errors: SR_ERR_INVALID_ARG, SR_ERR_CUDA. */
+ * tensor map), the others aggregate all D; NCC costs are computed only in
+ * the 32-disparity chunks some tile reads.  sr_get_buffer's cost volumes are
+ * therefore partial after this call.  Asynchronous; the first call
+ * allocates three ints per tile, zeroes the cost volumes and builds the
+ * tensor maps.  Errors: SR_ERR_INVALID_ARG, SR_ERR_CUDA. */
 sr_status sr_match_restricted(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                               int pitch_bytes, const int16_t *d_centre, int radius,
                               float *d_disp, int16_t *d_wta_or_null);

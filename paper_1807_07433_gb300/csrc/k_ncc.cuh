@@ -59,7 +59,8 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
                                          const float *__restrict__ inv_l,
                                          const float *__restrict__ mu_r,
                                          const float *__restrict__ inv_r, int W, int H,
-                                         VT *__restrict__ vol, int x0, int y0) {
+                                         VT *__restrict__ vol, int x0, int y0,
+                                         int dlo = 0, int dhi = D - 1) {
     using S = NccSmem<RN, D>;
     constexpr int B = S::B, FW = S::FW, SW = S::SW, TH = S::TH, XW = S::XW;
     constexpr int DC = D < 32 ? D : 32;          // disparity chunk held in registers
@@ -128,6 +129,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
 
 #pragma unroll 1
     for (int d0 = 0; d0 < D; d0 += DC) {
+        if (d0 + DC <= dlo || d0 > dhi) continue;   // no aggregation tile reads this chunk
         float acc[DC];
 #pragma unroll
         for (int i = 0; i < DC; ++i) acc[i] = 0.0f;
@@ -170,10 +172,16 @@ __global__ void __launch_bounds__(kNccThreads)
 k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
       const float *__restrict__ mu_l, const float *__restrict__ inv_l,
       const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
-      VT *__restrict__ vol) {
+      VT *__restrict__ vol, const int2 *__restrict__ range) {
     __shared__ NccSmem<RN, D> sm;
+    int dlo = 0, dhi = D - 1;
+    if (range) {   // restricted search: the disparities the tile's readers need
+        const int2 r = range[blockIdx.y * gridDim.x + blockIdx.x];
+        dlo = r.x;
+        dhi = r.y;
+    }
     ncc_tile<RN, D, TARGET, VT>(sm, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol,
-                                blockIdx.x * kNccTX, blockIdx.y * kNccTY);
+                                blockIdx.x * kNccTX, blockIdx.y * kNccTY, dlo, dhi);
 }
 
 // Persistent batched form: CTA b handles work items b, b + gridDim.x, ...
@@ -208,12 +216,13 @@ k_ncc_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
 template <int RN, int D, typename VT>
 cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
-                         const float *inv_r, int W, int H, VT *vol, cudaStream_t st) {
+                         const float *inv_r, int W, int H, VT *vol, cudaStream_t st,
+                         const int2 *range) {
     const dim3 grid((W + kNccTX - 1) / kNccTX, (H + kNccTY - 1) / kNccTY);
     if (target)
-        k_ncc<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
+        k_ncc<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, range);
     else
-        k_ncc<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol);
+        k_ncc<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, range);
     return cudaGetLastError();
 }
 
@@ -248,9 +257,9 @@ template <int D, typename VT>
 cudaError_t ncc_launch_d(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
                          const float *inv_r, int W, int H, int ncc_r, VT *vol,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int2 *range) {
     SR_NCC_RN_SWITCH(ncc_r, return (ncc_launch_t<RN_, D, VT>(target, left, pitch, rw, mu_l, inv_l,
-                                                             mu_r, inv_r, W, H, vol, st)))
+                                                             mu_r, inv_r, W, H, vol, st, range)))
     return cudaErrorInvalidValue;
 }
 

@@ -43,7 +43,32 @@ k_tile_bands(AggWin win, int W, int H, int align, int *__restrict__ band) {
     }
 }
 
+__global__ void k_ncc_ranges(const int *__restrict__ band, int tx, int ty, int D, int reach_y,
+                             int2 *__restrict__ range) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tx * ty) return;
+    const int bx = t % tx, by = t / tx;
+    int lo = D, hi = -1;
+    // aggregation tiles within one tile column (agg_r < 32) and reach_y tile
+    // rows read this tile's costs
+    for (int y = max(by - reach_y, 0); y <= min(by + reach_y, ty - 1); ++y)
+        for (int x = max(bx - 1, 0); x <= min(bx + 1, tx - 1); ++x) {
+            const int b = band[y * tx + x];
+            if (b < 0) { lo = 0; hi = D - 1; }
+            else { lo = min(lo, b); hi = max(hi, b + kBandD - 1); }
+        }
+    range[t] = make_int2(lo, hi);
+}
+
 }  // namespace
+
+cudaError_t launch_ncc_ranges(const int *band, int W, int H, int D, int agg_r, int2 *range,
+                              cudaStream_t st) {
+    const int tx = (W + kTileTX - 1) / kTileTX, ty = (H + kTileTY - 1) / kTileTY;
+    const int reach_y = (agg_r + kTileTY - 1) / kTileTY;
+    k_ncc_ranges<<<(tx * ty + 255) / 256, 256, 0, st>>>(band, tx, ty, D, reach_y, range);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tile_bands(const AggWin &win, int W, int H, int align, int *band,
                               cudaStream_t st) {

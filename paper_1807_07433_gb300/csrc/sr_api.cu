@@ -13,23 +13,23 @@
 #include "sr_ctx.cuh"
 
 namespace sr {
-cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d16_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d16_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d16_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d16_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d32_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d32_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d64_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d64_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st);
+cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 
 cudaError_t launch_agg_band_f32(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
@@ -91,11 +91,11 @@ bool agg_supported(int D, int agg_r) {
 cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
                        const float *mu_l, const float *inv_l, const float *mu_r,
                        const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int2 *range) {
     switch (D) {
-        case 16: SR_VT_DISPATCH(launch_ncc, 16, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st)
-        case 32: SR_VT_DISPATCH(launch_ncc, 32, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st)
-        case 64: SR_VT_DISPATCH(launch_ncc, 64, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st)
+        case 16: SR_VT_DISPATCH(launch_ncc, 16, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st, range)
+        case 32: SR_VT_DISPATCH(launch_ncc, 32, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st, range)
+        case 64: SR_VT_DISPATCH(launch_ncc, 64, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st, range)
         default: return cudaErrorInvalidValue;
     }
 }
@@ -197,7 +197,8 @@ void free_all(sr_ctx *c) {
     void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
                     c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
                     c->stage_disp, c->d_err, c->g_vol, c->g_wsum, c->g_rw, c->g_partial,
-                    c->f_pairs, c->f_has, c->f_counts, c->f_model, c->f_partial, c->band};
+                    c->f_pairs, c->f_has, c->f_counts, c->f_model, c->f_partial, c->band,
+                    c->nrange};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)
@@ -474,10 +475,21 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
         if (!c->band) {
             const size_t tiles = (size_t)sr::ceil_div(W, sr::kAggTileX) * sr::ceil_div(H, sr::kAggTileY);
             SR_TRY(c, dalloc(&c->band, tiles), "cudaMalloc(bands)");
+            SR_TRY(c, dalloc(&c->nrange, tiles), "cudaMalloc(ranges)");
+        }
+        if (!c->vols_zeroed) {
+            // costs outside a tile's NCC range are not written; the band boxes
+            // may read such entries next to the image's ends (with zero weight),
+            // so they must hold finite values
+            const size_t vb = (size_t)W * H * D * sr::vol_elem_bytes(p.vol_dtype);
+            SR_TRY(c, cudaMemsetAsync(c->vol_l, 0, vb, st), "cudaMemset(volume)");
+            SR_TRY(c, cudaMemsetAsync(c->vol_r, 0, vb, st), "cudaMemset(volume)");
+            c->vols_zeroed = true;
         }
         win.band = c->band;
         const int align = (int)(16 / sr::vol_elem_bytes(p.vol_dtype));
         SR_TRY(c, sr::launch_tile_bands(win, W, H, align, c->band, st), "tile bands");
+        SR_TRY(c, sr::launch_ncc_ranges(c->band, W, H, D, p.agg_radius, c->nrange, st), "ncc ranges");
     }
     c->matched = false;
     c->timed = false;
@@ -487,11 +499,12 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
     SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
                                c->mu_r, c->inv_r, st),
            "stats");
+    const int2 *nrange = banded ? c->nrange : nullptr;
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st),
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st, nrange),
            "ncc_ref");
     SR_TRY(c, sr::launch_ncc(true, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, p.vol_dtype, st),
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, p.vol_dtype, st, nrange),
            "ncc_tgt");
     if (banded) {
         SR_TRY(c, sr::launch_agg_band(&c->tmap_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H,

@@ -40,7 +40,8 @@ struct sr_ctx {
     double *g_partial = nullptr;     // block partials, then 3 results at the end
     // sr_match_restricted: per-tile bands and tensor maps of the two volumes
     int *band = nullptr;
-    bool tmaps = false;
+    int2 *nrange = nullptr;          // per-tile NCC disparity ranges
+    bool tmaps = false, vols_zeroed = false;
     CUtensorMap tmap_l{}, tmap_r{};
     // sr_fit_alpha / sr_fit_roll scratch, grown on demand
     int fit_cap = 0;                 // hypotheses the buffers hold

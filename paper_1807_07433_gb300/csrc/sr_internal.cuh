@@ -69,10 +69,12 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
 // rounded to nearest on store).  target = false: reference volume
 // c(u,v,d) = NCC(left block u, warped-target block u-d); target = true:
 // target volume c(u,v,d) = NCC(left block u+d, warped-target block u).
+//   range (nullable): per 32 x 4 tile, the disparities {lo, hi} that some
+//   reader of the tile needs; chunks of disparities outside are not computed
 cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
                        const float *mu_l, const float *inv_l, const float *mu_r,
                        const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
-                       cudaStream_t st);
+                       cudaStream_t st, const int2 *range = nullptr);
 
 // Bounded-wait settings of the aggregation kernel.  err (nullable) receives 1
 // when a wait for a cost-row copy runs out after wait_cycles SM clocks;
@@ -122,6 +124,11 @@ cudaError_t launch_agg_band(const void *tmap, int vt, const uint8_t *guide_u8, i
 // band[t] = the aligned start of a kBandD slice holding every window of the
 // tile (align: 16 bytes of the stored type), or -1.
 cudaError_t launch_tile_bands(const AggWin &win, int W, int H, int align, int *band,
+                              cudaStream_t st);
+// The NCC range of every 32 x 4 tile under the restricted search: the union
+// of the disparity slices of the aggregation tiles whose windows (radius
+// agg_r) reach it, [0, D-1] when one of them needs all D.
+cudaError_t launch_ncc_ranges(const int *band, int W, int H, int D, int agg_r, int2 *range,
                               cudaStream_t st);
 
 // Eq. 11 check with tolerance, then Sec. II-C post-processing.
