@@ -58,10 +58,14 @@ struct AggCfg {
     // copy needs for its destination
     static constexpr int RINGS = (int)(((RING * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
     static constexpr int WRING = kAggTY * WS * kAggTX;  // floats per weight slot
+    // weight-ring slots: two let the warps of a CTA compute the next row's
+    // weights while others still read the current ones; a one-warp CTA
+    // (D = 16) runs in order anyway, so one slot saves the shared memory
+    static constexpr int WSL = NW > 1 ? 2 : 1;
     // shared memory, in bytes: [cost ring | weight ring] (reused by the
     // epilogue transpose), guide tile, weight sums, two mbarriers
     static constexpr size_t RINGB = 2 * (size_t)RINGS * sizeof(VT);
-    static constexpr size_t RINGSB = RINGB + 2 * (size_t)WRING * sizeof(float);
+    static constexpr size_t RINGSB = RINGB + WSL * (size_t)WRING * sizeof(float);
     static constexpr size_t EPIB = (size_t)kAggPix * (D + 1) * sizeof(float);
     static constexpr size_t UNIONB = ((RINGSB > EPIB ? RINGSB : EPIB) + 15) / 16 * 16;
     static constexpr int GUIDE = TYE * TXE;
@@ -70,6 +74,8 @@ struct AggCfg {
     static constexpr size_t SMEM = UNIONB + sizeof(float) * ((GUIDE + 3) / 4 * 4 + kAggPix) +
                                    2 * sizeof(unsigned long long) +
                                    sizeof(int) * (kStartSmem + 4);
+    // kernels that do not walk a batch work list leave out its prefix array
+    static constexpr size_t SMEM_SINGLE = SMEM - sizeof(int) * kStartSmem;
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
 };
 
@@ -169,9 +175,10 @@ __device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT> &sm) {
 //
 // BAND: the ring holds the D = kBandD disparities [dlo, dlo + D) of each pixel,
 // loaded as one 2-D tensor-map box per row (tmap); otherwise the D
-// disparities of the volume, one bulk copy per row.  win restricts the WTA
-// and Eq. 12 of each pixel to its window (see AggWin).
-template <int R, int D, bool GU8, typename VT, bool BAND = false>
+// disparities of the volume, one bulk copy per row.  WIN: win restricts the
+// WTA and Eq. 12 of each pixel to its window (see AggWin); a compile-time
+// choice, so that the full search keeps its own code.
+template <int R, int D, bool GU8, typename VT, bool BAND = false, bool WIN = BAND>
 __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &ph,
                                          const VT *__restrict__ vol, const uint8_t *__restrict__ gl,
                                          int pitch, const float *__restrict__ gf, int W, int H,
@@ -226,7 +233,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
 #pragma unroll
     for (int k = 0; k < 4 / C::NW; ++k) wacc[k] = 0.0f;
     auto make_weights = [&](int j) {
-        float *wslot = wring + (j & 1) * C::WRING;
+        float *wslot = wring + (j % C::WSL) * C::WRING;
 #pragma unroll
         for (int k = 0; k < 4 / C::NW; ++k) {
             const int py = warp + k * C::NW;
@@ -255,7 +262,14 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         }
     };
 
-    // ---- prologue: guide tile, zeroed columns, first row --------------------
+    // ---- prologue: first row in flight, guide tile, zeroed columns ---------
+    // (the copy writes only the in-image columns of slot 0, the zeroing only
+    // the others; in a persistent CTA the barrier before this tile ordered
+    // the previous epilogue's reads of this memory)
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        issue_row(0);
+    }
     for (int i = tid; i < C::GUIDE; i += C::NT) {
         const int r = i / C::TXE, c = i % C::TXE;
         const int y = y0 - R + r, x = x0 - R + c;
@@ -271,11 +285,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        issue_row(0);
-    }
-    make_weights(0);
+    if (C::WSL == 2) make_weights(0);
     __syncthreads();
 
     // ---- main loop: stream the tile's source rows --------------------------
@@ -297,13 +307,17 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 issue_row(j + 1);
             }
-            make_weights(j + 1);
+            if (C::WSL == 2) make_weights(j + 1);
+        }
+        if (C::WSL == 1) {   // the single slot was last read before the previous barrier
+            make_weights(j);
+            __syncthreads();
         }
         const int y = y0 - R + j;
         if (y >= 0 && y < H) {
             mbar_wait(bars + (j & 1), (ph >> (j & 1)) & 1u, wait_cycles, err);
             const VT *rs = ring + (j & 1) * C::RINGS + bx * D + 2 * sl;
-            const float *ws = wring + (j & 1) * C::WRING + bx;
+            const float *ws = wring + (j % C::WSL) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
 #pragma unroll
             for (int i = 0; i < kAggPX + 2 * R; ++i)
@@ -356,22 +370,22 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         const size_t o = (size_t)v * W + u;
         // search window in slice indices: 0..D-1, or the pixel's window
         int lo = 0, hi = D - 1;
-        if (win.radius >= 0) {
-            int cc = win.centre ? win.centre[o] : win.centre_const;
-            cc = min(max(cc, 0), win.dfull - 1);
-            lo = max(max(cc - win.radius, 0) - dlo, 0);         // the clamps only
-            hi = min(min(cc + win.radius, win.dfull - 1) - dlo, D - 1);   // keep bad input in bounds
-            if (hi < lo) hi = lo;
-        }
-        int best = lo;
-        float cb = e[lo];
-        if (lo == 0 && hi == D - 1) {
+        int best = 0;
+        float cb = e[0];
+        if (!WIN) {
 #pragma unroll 8
             for (int d = 1; d < D; ++d) {
                 const float c = e[d];
                 if (c > cb) { cb = c; best = d; }
             }
         } else {
+            int cc = win.centre ? win.centre[o] : win.centre_const;
+            cc = min(max(cc, 0), win.dfull - 1);
+            lo = max(max(cc - win.radius, 0) - dlo, 0);         // the clamps only
+            hi = min(min(cc + win.radius, win.dfull - 1) - dlo, D - 1);   // keep bad input in bounds
+            if (hi < lo) hi = lo;
+            best = lo;
+            cb = e[lo];
             for (int d = lo + 1; d <= hi; ++d) {
                 const float c = e[d];
                 if (c > cb) { cb = c; best = d; }
@@ -401,21 +415,21 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
     }
 }
 
-template <int R, int D, bool GU8, typename VT>
+template <int R, int D, bool GU8, typename VT, bool WIN>
 __global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
 k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
           const float *__restrict__ gf, int W, int H, float kd, float kr,
           int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
           int *__restrict__ err, long long wait_cycles, int withhold_last, AggWin win) {
     // restricted search: tiles of the band kernel are not this kernel's
-    if (win.band && win.band[blockIdx.y * gridDim.x + blockIdx.x] >= 0) return;
+    if (WIN && win.band && win.band[blockIdx.y * gridDim.x + blockIdx.x] >= 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const AggSmem<R, D, VT> sm{smem_raw};
     agg_init_barriers(sm);
     unsigned ph = 0;
-    agg_tile<R, D, GU8, VT>(sm, ph, vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, err,
-                            wait_cycles, withhold_last, blockIdx.x * kAggTX, blockIdx.y * kAggTY,
-                            nullptr, 0, win);
+    agg_tile<R, D, GU8, VT, false, WIN>(sm, ph, vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg,
+                                        err, wait_cycles, withhold_last, blockIdx.x * kAggTX,
+                                        blockIdx.y * kAggTY, nullptr, 0, win);
 }
 
 // Band kernel of the restricted search: the tile's kBandD-disparity slice
@@ -479,16 +493,17 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
     }
 }
 
-template <int R, int D, typename VT>
+template <int R, int D, typename VT, bool WIN>
 cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
                          const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
     using C = AggCfg<R, D, VT>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
-    auto k = gl ? k_agg_wta<R, D, true, VT> : k_agg_wta<R, D, false, VT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    auto k = gl ? k_agg_wta<R, D, true, VT, WIN> : k_agg_wta<R, D, false, VT, WIN>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_SINGLE);
     if (e != cudaSuccess) return e;
-    k<<<grid, C::NT, C::SMEM, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
+    k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
                                     dbg.wait_cycles, dbg.withhold_last, win);
     return cudaGetLastError();
 }
@@ -501,9 +516,10 @@ cudaError_t agg_band_launch_t(const CUtensorMap &tmap, const uint8_t *gl, int pi
     using C = AggCfg<R, kBandD, VT>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
     auto k = gl ? k_agg_band<R, true, VT> : k_agg_band<R, false, VT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_SINGLE);
     if (e != cudaSuccess) return e;
-    k<<<grid, C::NT, C::SMEM, st>>>(tmap, gl, pitch, gf, W, H, kd, kr, lbl, dsub, dbg.err,
+    k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(tmap, gl, pitch, gf, W, H, kd, kr, lbl, dsub, dbg.err,
                                     dbg.wait_cycles, win);
     return cudaGetLastError();
 }
@@ -541,12 +557,12 @@ int agg_occ_t() {
         default: break;                              \
     }
 
-template <int D, typename VT>
+template <int D, typename VT, bool WIN>
 cudaError_t agg_launch_d(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub,
                          float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
-    SR_AGG_R_SWITCH(agg_r, return (agg_launch_t<R_, D, VT>(vol, gl, pitch, gf, W, H, kd, kr, lbl,
-                                                           dsub, agg, dbg, st, win)))
+    SR_AGG_R_SWITCH(agg_r, return (agg_launch_t<R_, D, VT, WIN>(vol, gl, pitch, gf, W, H, kd, kr,
+                                                                lbl, dsub, agg, dbg, st, win)))
     return cudaErrorInvalidValue;
 }
 

@@ -67,6 +67,16 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     const int tid = threadIdx.x;
     const int WE = W + D - 1;
 
+    // This pixel's fixed-block statistics, loaded first so that their latency
+    // overlaps the staging below.
+    const int tx = tid % kNccTX, ty = tid / kNccTX;
+    const int u = x0 + tx, v = y0 + ty;
+    const bool inside = u < W && v < H;
+    const size_t rowo = (size_t)(inside ? v : 0) * WE;
+    const int uc = inside ? u : 0;
+    const float m = TARGET ? mu_r[rowo + uc + D - 1] : mu_l[rowo + uc];
+    const float inv_f0 = TARGET ? inv_r[rowo + uc + D - 1] : inv_l[rowo + uc];
+
     // Stage the fixed and sliding tiles (clamp-to-edge).
     const int fx0 = x0 - RN;
     const int sx0 = TARGET ? x0 - RN : x0 - RN - (D - 1);
@@ -97,21 +107,15 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     }
     __syncthreads();
 
-    const int tx = tid % kNccTX, ty = tid / kNccTX;
-    const int u = x0 + tx, v = y0 + ty;
-    if (u >= W || v >= H) return;
+    if (!inside) return;
 
     // Statistics rows (block centres extended by D-1 columns, see launch_stats):
     // the fixed block sits at u, the sliding block at u+d (target) / u-d (reference).
-    const size_t rowo = (size_t)v * WE;
-    const float *mu_f = TARGET ? mu_r + rowo + u + D - 1 : mu_l + rowo + u;
-    const float *inv_fp = TARGET ? inv_r + rowo + u + D - 1 : inv_l + rowo + u;
     // sliding centre of disparity d at smem index base + so, so = d or -d
     const float *mu_s_row = &sm.smu_s[ty][TARGET ? tx : tx + D - 1];
     const float *inv_s_row = &sm.sinv_s[ty][TARGET ? tx : tx + D - 1];
 
     // Centred fixed block and the sum of its (rounded) centred values.
-    const float m = *mu_f;
     float a[B][B];
     float sa = 0.0f;
 #pragma unroll
@@ -124,7 +128,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
 
     // n/(n sigma_f) of the fixed block (Eq. 3 divides n*cov by n*sigma_f*sigma_s).
     constexpr float n = (float)(B * B);
-    const float inv_f = n * *inv_fp;
+    const float inv_f = n * inv_f0;
     VT *out = vol + ((size_t)v * W + u) * D;
 
 #pragma unroll 1

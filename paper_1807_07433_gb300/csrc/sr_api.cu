@@ -32,6 +32,15 @@ cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, co
 cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
 cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 
+cudaError_t launch_aggw_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
 cudaError_t launch_agg_band_f32(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 cudaError_t launch_agg_band_f16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 cudaError_t launch_agg_band_bf16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
@@ -106,6 +115,14 @@ cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pit
                        const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
     const float log2e = 1.4426950408889634f;
     const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
+    if (win.radius >= 0) {   // restricted search: the windowed kernels
+        switch (D) {
+            case 16: SR_VT_DISPATCH(launch_aggw, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+            case 32: SR_VT_DISPATCH(launch_aggw, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+            case 64: SR_VT_DISPATCH(launch_aggw, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (D) {
         case 16: SR_VT_DISPATCH(launch_agg, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
         case 32: SR_VT_DISPATCH(launch_agg, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
