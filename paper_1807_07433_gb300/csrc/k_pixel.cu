@@ -222,7 +222,114 @@ __global__ void k_xyz(const float *__restrict__ disp, int W, int H, float f, flo
 
 dim3 grid_for(int w, int h) { return dim3((w + kBX - 1) / kBX, (h + kBY - 1) / kBY); }
 
+// Fused perspective transformation (Sec. II-A) and block statistics (Eqs.
+// 4-5) of both images, for one 32 x 8 tile of extended block centres: the
+// tile's left rows and its warped-target rows (each with the block halo,
+// clamp-to-edge) are staged in shared memory once, the row shifts once per
+// row; every statistic is then computed from shared memory with the same
+// operations in the same order as stats_left_px / stats_right_px, and the
+// warped image is written for the columns this tile owns.
+template <int RN>
+__global__ void __launch_bounds__(kBX * kBY)
+k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch, int W,
+       int H, int D, double alpha0, double alpha1, double delta, float *__restrict__ rw,
+       float *__restrict__ mu_l, float *__restrict__ inv_l, float *__restrict__ mu_r,
+       float *__restrict__ inv_r) {
+    constexpr int B = 2 * RN + 1, TH = kBY + 2 * RN, TW = kBX + 2 * RN;
+    constexpr int n = B * B;
+    __shared__ int s_l[TH][TW];           // left intensities
+    __shared__ float s_r[TH][TW];         // warped target intensities
+    __shared__ int s_k[TH];               // row shift: integer part
+    __shared__ float s_w[TH];             // row shift: fraction
+    const int WE = W + D - 1;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
+    const int xr0 = x0 - (D - 1);         // first target-block centre of the tile
+    if (tid < TH) {
+        const int y = clampi(y0 - RN + tid, 0, H - 1);
+        const double sh = alpha0 + alpha1 * (double)y - delta;
+        double k = floor(sh);
+        s_w[tid] = (float)(sh - k);
+        k = fmin(fmax(k, -2.0 * W - 2.0), 2.0 * W + 2.0);   // beyond this every read clamps
+        s_k[tid] = (int)k;
+    }
+    __syncthreads();
+    for (int i = tid; i < TH * TW; i += kBX * kBY) {
+        const int r = i / TW, c = i % TW;
+        const int y = clampi(y0 - RN + r, 0, H - 1);
+        s_l[r][c] = left[(size_t)y * pitch + clampi(x0 - RN + c, 0, W - 1)];
+        const int x = clampi(xr0 - RN + c, 0, W - 1);
+        const uint8_t *row = right + (size_t)y * pitch;
+        const float a = row[clampi(x - s_k[r], 0, W - 1)];
+        const float b = row[clampi(x - s_k[r] - 1, 0, W - 1)];
+        s_r[r][c] = fmaf(s_w[r], b - a, a);              // (1-w) a + w b
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int xi = x0 + tx, v = y0 + ty;
+    if (xi >= WE || v >= H) return;
+    // left block at centre xi (exact integer sums)
+    {
+        unsigned su = 0, s2 = 0;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                const unsigned val = (unsigned)s_l[ty + j][tx + i];
+                su += val;
+                s2 += val * val;
+            }
+        const long long q = (long long)n * s2 - (long long)su * su;   // n^2 var, exact
+        const float var = (float)q / (float)(n * n);
+        inv_l[(size_t)v * WE + xi] = (var < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)q);
+        mu_l[(size_t)v * WE + xi] = (float)su / (float)n;
+    }
+    // warped-target block at centre xi - (D-1): mean from row sums of
+    // (value - 128), then centred squares
+    {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            float rs = 0.0f;
+#pragma unroll
+            for (int i = 0; i < B; ++i) rs += s_r[ty + j][tx + i] - kNccOffset;
+            s += rs;
+        }
+        const float m = kNccOffset + s / (float)n;
+        float q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                const float c = s_r[ty + j][tx + i] - m;
+                q = fmaf(c, c, q);
+            }
+        inv_r[(size_t)v * WE + xi] = (q / (float)n < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)n * q);
+        mu_r[(size_t)v * WE + xi] = m;
+    }
+    // the warped image, at the target columns this tile owns
+    const int xr = xi - (D - 1);
+    if (xr >= 0) rw[(size_t)v * W + xr] = s_r[ty + RN][tx + RN];
+}
+
 }  // namespace
+
+cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, int W, int H, int D,
+                        int ncc_r, double alpha0, double alpha1, double delta, float *rw,
+                        float *mu_l, float *inv_l, float *mu_r, float *inv_r, cudaStream_t st) {
+    const dim3 grid = grid_for(W + D - 1, H), block(kBX, kBY);
+    switch (ncc_r) {
+#define SR_PREP(RN_)                                                                          \
+    case RN_:                                                                                 \
+        k_prep<RN_><<<grid, block, 0, st>>>(left, right, pitch, W, H, D, alpha0, alpha1, delta, \
+                                            rw, mu_l, inv_l, mu_r, inv_r);                     \
+        break;
+        SR_PREP(1) SR_PREP(2) SR_PREP(3) SR_PREP(4) SR_PREP(5)
+#undef SR_PREP
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_warp(const uint8_t *right, int pitch, int W, int H, double alpha0,
                         double alpha1, double delta, float *rw, cudaStream_t st) {

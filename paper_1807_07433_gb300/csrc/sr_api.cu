@@ -198,7 +198,7 @@ int agg_batch_occupancy(int D, int agg_r, int vt) {
 
 namespace {
 
-const char *const kStageNames = "warp,stats,ncc_ref,ncc_tgt,agg_ref,agg_tgt,lrc_post";
+const char *const kStageNames = "prep,ncc_ref,ncc_tgt,agg_ref,agg_tgt,lrc_post";
 
 }  // namespace
 
@@ -304,7 +304,7 @@ const char *sr_stage_names(void) { return kStageNames; }
 
 int sr_kernels_per_match(const sr_ctx *c) {
     (void)c;
-    return 8;   // warp, 2x stats, 2x ncc, 2x agg, lrc_post
+    return 6;   // prep (warp + statistics), 2x ncc, 2x agg, lrc_post
 }
 
 sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
@@ -431,12 +431,9 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     c->matched = false;
     c->timed = false;
     SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_warp(d_right, pitch_bytes, W, H, c->alpha0, c->alpha1, c->delta, c->rw, st),
-           "warp");
-    SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
-                               c->mu_r, c->inv_r, st),
-           "stats");
+    SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
+                              c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
+           "prep");
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
                              c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st),
@@ -511,11 +508,9 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
     c->matched = false;
     c->timed = false;
     const sr::AggDebug dbg = agg_debug(c);
-    SR_TRY(c, sr::launch_warp(d_right, pitch_bytes, W, H, c->alpha0, c->alpha1, c->delta, c->rw, st),
-           "warp");
-    SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
-                               c->mu_r, c->inv_r, st),
-           "stats");
+    SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
+                              c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
+           "prep");
     const int2 *nrange = banded ? c->nrange : nullptr;
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
                              c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st, nrange),
@@ -599,11 +594,9 @@ sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right
     }
     cudaStream_t st = c->st;
     c->matched = false;   // the context's scratch no longer holds the last sr_match
-    SR_TRY(c, sr::launch_warp(d_right, pitch_bytes, W, H, c->alpha0, c->alpha1, c->delta, c->rw, st),
-           "warp");
-    SR_TRY(c, sr::launch_stats(d_left, pitch_bytes, c->rw, W, H, D, p.ncc_radius, c->mu_l, c->inv_l,
-                               c->mu_r, c->inv_r, st),
-           "stats");
+    SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
+                              c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
+           "prep");
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
                              c->inv_r, W, H, D, p.ncc_radius, cost, sr::kVolF32, st),
            "ncc_ref");

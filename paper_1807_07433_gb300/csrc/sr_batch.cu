@@ -20,7 +20,7 @@
 //     capture streams, largest first, so that one pair's kernels fill the
 //     tails of another's; still descriptor-driven, so the graph replays with
 //     new images and planes as long as the sequence of sizes repeats;
-//   C (variants 6-7): per pair, the eight kernels of sr_match itself with the
+//   C (variants 6-7): per pair, the six kernels of sr_match itself with the
 //     pair's pointers and plane as kernel parameters, on 1 or 4 forked capture
 //     streams, largest first.  The graph holds the parameters, so a call with
 //     other pointers or planes re-captures it and updates the executable graph
@@ -217,9 +217,8 @@ cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     const sr::PairDesc &P = b->h_desc[k];
     const sr::AggDebug dbg = agg_debug(c);
     cudaError_t e;
-    if ((e = sr::launch_warp(P.right, P.pitch, P.W, P.H, P.alpha0, P.alpha1, P.delta, P.rw, st)) != cudaSuccess) return e;
-    if ((e = sr::launch_stats(P.left, P.pitch, P.rw, P.W, P.H, D, p.ncc_radius, P.mu_l, P.inv_l,
-                              P.mu_r, P.inv_r, st)) != cudaSuccess) return e;
+    if ((e = sr::launch_prep(P.left, P.right, P.pitch, P.W, P.H, D, p.ncc_radius, P.alpha0,
+                             P.alpha1, P.delta, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, st)) != cudaSuccess) return e;
     if ((e = sr::launch_ncc(false, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
                             P.H, D, p.ncc_radius, P.vol_l, p.vol_dtype, st)) != cudaSuccess) return e;
     if ((e = sr::launch_ncc(true, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
@@ -515,7 +514,7 @@ sr_status sr_batch_info(sr_ctx *c, char *buf, size_t size) {
              b->graph_n, b->variant, sched, per_pair(b->variant) ? 1 : ((b->variant & 1) ? 2 : 1),
              per_pair(b->variant) ? 1 : (b->variant >> 1) & 1,
              per_pair(b->variant) ? pair_streams(b->variant) : 1,
-             sched_c(b->variant) ? 8 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
+             sched_c(b->variant) ? 6 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
              sr::ncc_batch_occupancy(D, c->p.ncc_radius, c->p.vol_dtype),
              sr::agg_batch_occupancy(D, c->p.agg_radius, c->p.vol_dtype), b->sms, ms,
              b->pool_bytes);

@@ -65,6 +65,12 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
                          int ncc_r, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
                          cudaStream_t st);
 
+// launch_warp and launch_stats in one kernel (the same values): the warped
+// image rw and the four statistics arrays.
+cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, int W, int H, int D,
+                        int ncc_r, double alpha0, double alpha1, double delta, float *rw,
+                        float *mu_l, float *inv_l, float *mu_r, float *inv_r, cudaStream_t st);
+
 // Eq. 3 cost volume [H][W][D], stored as vt (VolType; FP32 arithmetic,
 // rounded to nearest on store).  target = false: reference volume
 // c(u,v,d) = NCC(left block u, warped-target block u-d); target = true:

@@ -105,9 +105,8 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const sr::AggDebug dbg;   // default bounded waits; no error word to report through
     const int Wi = p.width, Hi = p.height, Di = p.max_disp;
-    if (sr::launch_warp(d_right, pitch_bytes, Wi, Hi, alpha0, alpha1, delta, rw, st) != cudaSuccess ||
-        sr::launch_stats(d_left, pitch_bytes, rw, Wi, Hi, Di, p.ncc_radius, mu_l, inv_l, mu_r,
-                         inv_r, st) != cudaSuccess ||
+    if (sr::launch_prep(d_left, d_right, pitch_bytes, Wi, Hi, Di, p.ncc_radius, alpha0, alpha1,
+                        delta, rw, mu_l, inv_l, mu_r, inv_r, st) != cudaSuccess ||
         sr::launch_ncc(false, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
                        p.ncc_radius, vol_l, p.vol_dtype, st) != cudaSuccess ||
         sr::launch_ncc(true, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,

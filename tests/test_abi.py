@@ -48,7 +48,7 @@ def test_status_strings(lib):
     assert sr.status_name(sr.SR_ERR_UNSUPPORTED) == "SR_ERR_UNSUPPORTED"
     assert sr.status_name(99) == "SR_ERR_UNKNOWN"
     assert "sm_103a" in sr.sr_version()
-    assert sr.sr_stage_names()[0] == "warp"
+    assert sr.sr_stage_names()[0] == "prep"
 
 
 @pytest.mark.parametrize("field,value,status", [
