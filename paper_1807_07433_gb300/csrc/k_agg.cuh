@@ -229,9 +229,6 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
     // py the tap row is dyi = j - py.  w = exp(-r^2/gd^2 - dg^2/gr^2)
     // = exp2(-(r^2 kd + dg^2 kr)), zero for neighbours outside the image.
     // Warp k computes rows py = k, k + NW, ...; lane = pixel column.
-    float wacc[4 / C::NW];
-#pragma unroll
-    for (int k = 0; k < 4 / C::NW; ++k) wacc[k] = 0.0f;
     auto make_weights = [&](int j) {
         float *wslot = wring + (j % C::WSL) * C::WRING;
 #pragma unroll
@@ -246,7 +243,6 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
             const float *grow = guide + (py + dyi) * C::TXE + px;
             const float fy = (float)((dyi - R) * (dyi - R)) * kd;
             float *wout = wslot + (py * C::WS) * kAggTX + px;
-            float s = 0.0f;
 #pragma unroll
             for (int dxi = 0; dxi < C::WS; ++dxi) {
                 const float dg = grow[dxi] - gc;
@@ -256,9 +252,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
                     w = (rowok && x >= 0 && x < W) ? w : 0.0f;
                 }
                 wout[dxi * kAggTX] = w;
-                s += w;
             }
-            wacc[k] += s;
         }
     };
 
@@ -346,10 +340,21 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
     }
 
     // ---- epilogue: transpose (over the rings), WTA, parabola ----------------
-#pragma unroll
-    for (int k = 0; k < 4 / C::NW; ++k) {
-        const float s = wacc[k];
-        wsum[(warp + k * C::NW) * kAggTX + lane] = s > 0.0f ? s : 1.0f;
+    if (agg) {   // weight sums for the exported (normalised) volume only
+        for (int k = 0; k < 4 / C::NW; ++k) {
+            const int py = warp + k * C::NW, px = lane, u = x0 + px, v = y0 + py;
+            const float gc = guide[(py + R) * C::TXE + px + R];
+            float s = 0.0f;
+            for (int dyi = 0; dyi < C::WS; ++dyi)
+                for (int dxi = 0; dxi < C::WS; ++dxi) {
+                    const int x = u + dxi - R, y = v + dyi - R;
+                    if (u >= W || v >= H || x < 0 || x >= W || y < 0 || y >= H) continue;
+                    const float dg = guide[(py + dyi) * C::TXE + px + dxi] - gc;
+                    const float fy = (float)((dyi - R) * (dyi - R)) * kd;
+                    s += ex2_approx(-fmaf(dg * dg, kr, fmaf((float)((dxi - R) * (dxi - R)), kd, fy)));
+                }
+            wsum[py * kAggTX + px] = s > 0.0f ? s : 1.0f;
+        }
     }
     float *E = smem + warp * (32 * C::G) * (D + 1);     // this warp's pixels x D
 #pragma unroll
