@@ -243,3 +243,56 @@ def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
         m.match(dl, dr, wta=wta)
         sr.sr_synchronize(m.ctx)
         np.testing.assert_array_equal(wta.cpu().numpy(), good["wta"])
+
+
+EXTREME = [
+    # the widest frame the ABI accepts, fewer rows than the NCC block
+    synth.small(16384, 5, D=64, ncc_r=3, agg_r=5, seed=51, alpha1=0.02),
+    # a tall, narrow strip: fewer columns than the tile and the search range
+    synth.small(6, 300, D=64, ncc_r=2, agg_r=4, seed=52, alpha1=0.01),
+]
+
+
+@pytest.mark.parametrize("w", EXTREME, ids=lambda w: w.name)
+def test_extreme_aspect_ratios_match_oracle(w):
+    """Frame shapes at the edges of the tiling: aggregated volumes within
+    TOL_AGG, every label mismatch a near-tie, subpixel where well conditioned.
+    (In the 6-pixel strip clamp-to-edge blocks make near-ties common, about
+    0.7 % of its pixels, so the 99.9 % agreement gate of the benchmark
+    workload is not applied there.)"""
+    from paper_1807_07433_gb300 import sr
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right, keep_agg=True,
+                buffers=(("dsub", sr.SR_BUF_DSUB), ("agg_l", sr.SR_BUF_AGG_L),
+                         ("agg_r", sr.SR_BUF_AGG_R)))
+    o = run_oracle(w, left, right, ("agg_l", "agg_r", "lbl_l", "gap_l", "den_l", "dsub"))
+    np.testing.assert_allclose(g["agg_l"], o.agg_l, rtol=0, atol=TOL_AGG)
+    np.testing.assert_allclose(g["agg_r"], o.agg_r, rtol=0, atol=TOL_AGG)
+    agree, bad = label_report(g["wta"], o.lbl_l, o.gap_l)
+    assert bad == 0, (agree, bad)
+    if w.scene.W > 32:
+        assert agree >= AGREE_MIN
+    ok = (g["wta"] == o.lbl_l) & (o.gap_l >= TAU_TIE) & \
+        ((np.abs(o.den_l) >= DEN_MIN) | (o.den_l == 0))
+    assert np.abs(g["dsub"][ok] - o.dsub[ok]).max() <= TOL_DSUB
+
+
+def test_large_frame_sampled_pixels():
+    """A 4096x2160x64 frame (4.5 GB of FP32 volumes) at sampled pixels, corners
+    included."""
+    import oracle
+    w = synth.Workload("large 4096x2160", synth.Scene(4096, 2160, 30.0, 0.025, 40, True, 53),
+                       D=64, ncc_r=3, agg_r=5, gamma_d=4.0, gamma_r=12.0, delta=8.0)
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right)
+    H, W = left.shape
+    rng = np.random.default_rng(7)
+    us = np.concatenate([rng.integers(0, W, 120), [0, W - 1, 0, W - 1]])
+    vs = np.concatenate([rng.integers(0, H, 120), [0, 0, H - 1, H - 1]])
+    o = oracle.match_pixels(oracle_params(w), left, right, us, vs)
+    diff = g["wta"][vs, us] != o["lbl_l"]
+    assert np.all(o["gap_l"][diff] < TAU_TIE)
+    sharp = ~diff & (np.abs(o["den_l"]) >= DEN_MIN) & (o["gap_l"] >= TAU_TIE) & \
+        np.isfinite(o["dfull"]) & np.isfinite(g["dfull"][vs, us])
+    np.testing.assert_allclose(g["dfull"][vs, us][sharp], o["dfull"][sharp], rtol=0,
+                               atol=TOL_DSUB)
