@@ -264,13 +264,21 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         issue_row(0);
     }
-    for (int i = tid; i < C::GUIDE; i += C::NT) {
-        const int r = i / C::TXE, c = i % C::TXE;
-        const int y = y0 - R + r, x = x0 - R + c;
-        float g = 0.0f;
-        if (y >= 0 && y < H && x >= 0 && x < W)
-            g = GU8 ? (float)gl[(size_t)y * pitch + x] : gf[(size_t)y * W + x];
-        guide[i] = g;
+    {   // all loads of a thread first, then the stores: their latencies overlap
+        constexpr int NG = (C::GUIDE + C::NT - 1) / C::NT;
+        float g[NG];
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            const int i = tid + k * C::NT;
+            const int r = i / C::TXE, c = i % C::TXE;
+            const int y = y0 - R + r, x = x0 - R + c;
+            g[k] = 0.0f;
+            if (i < C::GUIDE && y >= 0 && y < H && x >= 0 && x < W)
+                g[k] = GU8 ? (float)gl[(size_t)y * pitch + x] : gf[(size_t)y * W + x];
+        }
+#pragma unroll
+        for (int k = 0; k < NG; ++k)
+            if (tid + k * C::NT < C::GUIDE) guide[tid + k * C::NT] = g[k];
     }
     if (!BAND && (xs > x0 - R || xe < x0 + kAggTX + R)) {
         for (int i = tid; i < 2 * C::RINGS; i += C::NT) {

@@ -254,15 +254,30 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
         s_k[tid] = (int)k;
     }
     __syncthreads();
-    for (int i = tid; i < TH * TW; i += kBX * kBY) {
-        const int r = i / TW, c = i % TW;
-        const int y = clampi(y0 - RN + r, 0, H - 1);
-        s_l[r][c] = left[(size_t)y * pitch + clampi(x0 - RN + c, 0, W - 1)];
-        const int x = clampi(xr0 - RN + c, 0, W - 1);
-        const uint8_t *row = right + (size_t)y * pitch;
-        const float a = row[clampi(x - s_k[r], 0, W - 1)];
-        const float b = row[clampi(x - s_k[r] - 1, 0, W - 1)];
-        s_r[r][c] = fmaf(s_w[r], b - a, a);              // (1-w) a + w b
+    {   // all loads of a thread first, then the stores: their latencies overlap
+        constexpr int NI = (TH * TW + kBX * kBY - 1) / (kBX * kBY);
+        int lv[NI];
+        float av[NI], bv[NI];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            const int i = min(tid + k * kBX * kBY, TH * TW - 1);
+            const int r = i / TW, c = i % TW;
+            const int y = clampi(y0 - RN + r, 0, H - 1);
+            lv[k] = left[(size_t)y * pitch + clampi(x0 - RN + c, 0, W - 1)];
+            const int x = clampi(xr0 - RN + c, 0, W - 1);
+            const uint8_t *row = right + (size_t)y * pitch;
+            av[k] = row[clampi(x - s_k[r], 0, W - 1)];
+            bv[k] = row[clampi(x - s_k[r] - 1, 0, W - 1)];
+        }
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            const int i = tid + k * kBX * kBY;
+            if (i < TH * TW) {
+                const int r = i / TW, c = i % TW;
+                s_l[r][c] = lv[k];
+                s_r[r][c] = fmaf(s_w[r], bv[k] - av[k], av[k]);   // (1-w) a + w b
+            }
+        }
     }
     __syncthreads();
     const int tx = threadIdx.x, ty = threadIdx.y;
