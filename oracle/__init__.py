@@ -31,8 +31,14 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, OpenMP, no FMA contraction)."""
+def build(force: bool = False, out: str | None = None, mutant: int = 0) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, no FMA contraction);
+    with mutant k > 0, into out with planted mistake k (pin tests only)."""
+    if mutant:
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", f"-DORC_MUTANT={int(mutant)}", _SRC, "-o", out, "-lm"]
+        subprocess.run(cmd, check=True)
+        return out
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
@@ -69,7 +75,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # ORC_LIB: a library built from oracle.c with a planted mistake
+            # (tests/test_oracle_mutants.py); otherwise the real one
+            lib = ctypes.CDLL(os.environ.get("ORC_LIB") or build())
             d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
             pp = ctypes.POINTER(_Params)
             sig = {

@@ -55,6 +55,16 @@ typedef struct {
 
 static int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
+/* Planted mistakes for the pin tests' own test (tests/test_oracle_mutants.py):
+ * built with -DORC_MUTANT=k, the library carries mistake k, one plausible
+ * slip each (a flipped sign or direction, a dropped term, an off-by-one, a
+ * wrong normaliser); the pins must catch every one.  The default build
+ * (ORC_MUTANT 0) has none. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+#define MUT(k) (ORC_MUTANT == (k))
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -91,9 +101,10 @@ void orc_warp(const orc_params *p, const uint8_t *ir, double *out) {
         const double w = s - k;
         const int ki = (int)k;
         for (int x = 0; x < W; ++x) {
-            const double a = ir[(size_t)v * W + clampi(x - ki, 0, W - 1)];
-            const double b = ir[(size_t)v * W + clampi(x - ki - 1, 0, W - 1)];
-            out[(size_t)v * W + x] = (1.0 - w) * a + w * b;
+            const int xa = MUT(1) ? x + ki : x - ki, xb = MUT(1) ? x + ki + 1 : x - ki - 1;
+            const double a = ir[(size_t)v * W + clampi(xa, 0, W - 1)];
+            const double b = ir[(size_t)v * W + clampi(xb, 0, W - 1)];
+            out[(size_t)v * W + x] = MUT(2) ? w * a + (1.0 - w) * b : (1.0 - w) * a + w * b;
         }
     }
 }
@@ -116,6 +127,7 @@ double orc_block_stats(const double *img, int W, int H, int r, int u, int v,
     }
     const double m = s / n;
     double var = s2 / n - m * m;          /* Eq. 4 / Eq. 5 under the root */
+    if (MUT(4)) var *= n / (n - 1.0);
     if (var < 0.0) var = 0.0;
     if (mu) *mu = m;
     if (sigma) *sigma = sqrt(var);
@@ -144,7 +156,7 @@ double orc_ncc(const double *L, const double *R, int W, int H, int r,
                    R[(size_t)y * W + clampi(ur + i, 0, W - 1)];
         }
     }
-    return (dot - n * mu_l * mu_r) / (n * sig_l * sig_r);
+    return ((MUT(3) ? dot : dot - n * mu_l * mu_r)) / (n * sig_l * sig_r);
 }
 
 /* Eqs. 8-10: bilateral aggregation of cost slice d at (u,v).
@@ -156,14 +168,14 @@ double orc_bilateral(const double *vol, int D, int d, const double *g, int W, in
     const double gc = g[(size_t)v * W + u];
     double num = 0.0, den = 0.0;
     for (int dy = -rho; dy <= rho; ++dy) {
-        const int y = v + dy;
+        const int y = MUT(6) ? clampi(v + dy, 0, H - 1) : v + dy;
         if (y < 0 || y >= H) continue;
         for (int dx = -rho; dx <= rho; ++dx) {
-            const int x = u + dx;
+            const int x = MUT(6) ? clampi(u + dx, 0, W - 1) : u + dx;
             if (x < 0 || x >= W) continue;
-            const double wd = exp(-(double)(dx * dx + dy * dy) / (gamma_d * gamma_d)); /* Eq. 9 */
+            const double wd = exp(-(double)(dx * dx + dy * dy) / ((MUT(5) ? 2.0 : 1.0) * gamma_d * gamma_d)); /* Eq. 9 */
             const double di = g[(size_t)y * W + x] - gc;
-            const double wr = exp(-(di * di) / (gamma_r * gamma_r));                  /* Eq. 10 */
+            const double wr = exp(-(di * di) / ((MUT(5) ? 2.0 : 1.0) * gamma_r * gamma_r));                  /* Eq. 10 */
             num += wd * wr * vol[((size_t)y * W + x) * D + d];
             den += wd * wr;
         }
@@ -181,14 +193,14 @@ static void bilateral_all_d(const double *vol, int D, const double *g, int W, in
     double den = 0.0;
     for (int d = 0; d < D; ++d) num[d] = 0.0;
     for (int dy = -rho; dy <= rho; ++dy) {
-        const int y = v + dy;
+        const int y = MUT(6) ? clampi(v + dy, 0, H - 1) : v + dy;
         if (y < 0 || y >= H) continue;
         for (int dx = -rho; dx <= rho; ++dx) {
-            const int x = u + dx;
+            const int x = MUT(6) ? clampi(u + dx, 0, W - 1) : u + dx;
             if (x < 0 || x >= W) continue;
-            const double wd = exp(-(double)(dx * dx + dy * dy) / (gamma_d * gamma_d));
+            const double wd = exp(-(double)(dx * dx + dy * dy) / ((MUT(5) ? 2.0 : 1.0) * gamma_d * gamma_d));
             const double di = g[(size_t)y * W + x] - gc;
-            const double wr = exp(-(di * di) / (gamma_r * gamma_r));
+            const double wr = exp(-(di * di) / ((MUT(5) ? 2.0 : 1.0) * gamma_r * gamma_r));
             const double *c = vol + ((size_t)y * W + x) * D;
             for (int d = 0; d < D; ++d) num[d] += wd * wr * c[d];
             den += wd * wr;
@@ -210,7 +222,7 @@ void orc_bilateral_slice(const double *slice, const double *g, int W, int H, int
 int orc_wta(const double *c, int D, double *gap) {
     int best = 0;
     for (int d = 1; d < D; ++d)
-        if (c[d] > c[best]) best = d;
+        if (MUT(7) ? c[d] >= c[best] : c[d] > c[best]) best = d;
     if (gap) {
         double second = -INFINITY;
         for (int d = 0; d < D; ++d)
@@ -233,7 +245,7 @@ double orc_parabola(const double *c, int D, int d, double *den) {
     const double q = 2.0 * cm + 2.0 * cp - 4.0 * c0;
     if (den) *den = q;
     if (!(q < 0.0)) return (double)d;
-    return (double)d + (cm - cp) / q;
+    return (double)d + (MUT(8) ? -1.0 : 1.0) * (cm - cp) / q;
 }
 
 /* Restricted search (the paper's Sec. IV plan: filter only the space around
@@ -244,13 +256,13 @@ double orc_parabola(const double *c, int D, int d, double *den) {
 static void search_window(int D, int centre, int radius, int *lo, int *hi) {
     const int c = clampi(centre, 0, D - 1);
     *lo = c - radius < 0 ? 0 : c - radius;
-    *hi = c + radius > D - 1 ? D - 1 : c + radius;
+    *hi = c + radius - (MUT(16) ? 1 : 0) > D - 1 ? D - 1 : c + radius - (MUT(16) ? 1 : 0);
 }
 
 int orc_wta_window(const double *c, int lo, int hi, double *gap) {
     int best = lo;
     for (int d = lo + 1; d <= hi; ++d)
-        if (c[d] > c[best]) best = d;
+        if (MUT(7) ? c[d] >= c[best] : c[d] > c[best]) best = d;
     if (gap) {
         double second = -INFINITY;
         for (int d = lo; d <= hi; ++d)
@@ -269,7 +281,7 @@ double orc_parabola_window(const double *c, int lo, int hi, int d, double *den) 
     const double q = 2.0 * cm + 2.0 * cp - 4.0 * c0;
     if (den) *den = q;
     if (!(q < 0.0)) return (double)d;
-    return (double)d + (cm - cp) / q;
+    return (double)d + (MUT(8) ? -1.0 : 1.0) * (cm - cp) / q;
 }
 
 /* Eq. 11 with a tolerance: pixel u of a row passes iff its match u - l_ref
@@ -277,12 +289,12 @@ double orc_parabola_window(const double *c, int lo, int hi, int d, double *den) 
 int orc_lr_valid(int u, int lref, const int32_t *ltar_row, double lr_thresh) {
     const int ur = u - lref;
     if (ur < 0) return 0;
-    return fabs((double)(lref - ltar_row[ur])) <= lr_thresh;
+    return fabs((double)(MUT(9) ? lref + ltar_row[ur] : lref - ltar_row[ur])) <= lr_thresh;
 }
 
 /* Sec. II-C: undo the perspective transform, d = d^s + alpha0 + alpha1*v - delta. */
 double orc_postprocess(const orc_params *p, double ds, int v) {
-    return ds + orc_row_shift(p, v);
+    return MUT(10) ? ds - orc_row_shift(p, v) : ds + orc_row_shift(p, v);
 }
 
 /* Sec. II-D: 3-D point of left pixel (u,v) with disparity dfull.
@@ -297,7 +309,7 @@ void orc_reconstruct(const orc_params *p, double dfull, int u, int v, double *X,
     const double z = p->f_px * p->baseline / dfull;
     *Z = z;
     *X = ((double)u - p->u0) * z / p->f_px;
-    *Y = ((double)v - p->v0) * z / p->f_px;
+    *Y = ((double)(MUT(11) ? u : v) - p->v0) * z / p->f_px;
 }
 
 /* Raw NCC volumes for rows [y0, y1).
@@ -314,7 +326,7 @@ static void cost_rows(const orc_params *p, const double *L, const double *R, int
             const size_t o = ((size_t)(v - row_base) * W + u) * D;
             for (int d = 0; d < D; ++d) {
                 if (cl) cl[o + d] = orc_ncc(L, R, W, H, p->ncc_r, u, u - d, v);
-                if (cr) cr[o + d] = orc_ncc(L, R, W, H, p->ncc_r, u + d, u, v);
+                if (cr) cr[o + d] = orc_ncc(L, R, W, H, p->ncc_r, MUT(12) ? u - d : u + d, u, v);
             }
         }
     }
@@ -648,7 +660,7 @@ int orc_grad(const orc_params *p, const double *il, const double *ir, const int3
                 /* through the weight w_k (guide = left image) */
                 const double gw = (ck[k] - cagg) / Wsum * wk[k] *
                                   (-2.0 * dk[k] / (p->gamma_r * p->gamma_r));
-                gL[(size_t)yk[k] * W + xk[k]] += gw;
+                gL[(size_t)yk[k] * W + xk[k]] += MUT(13) ? -gw : gw;
                 gL[(size_t)v * W + u] -= gw;
                 /* through the cost c_k = NCC(left block n_k, right block n_k - d) */
                 const double beta = wk[k] / Wsum;
@@ -761,7 +773,7 @@ int orc_fit_alpha(const float *disp, int W, int H, int n_hyp, const int32_t *pai
     }
     const double det = s0 * s2 - s1 * s1;
     if (det == 0.0) return -1;
-    alpha[1] = (s0 * t1 - s1 * t0) / det;
+    alpha[1] = (MUT(14) ? s1 * t0 - s0 * t1 : s0 * t1 - s1 * t0) / det;
     alpha[0] = (t0 - alpha[1] * s1) / s0;
     return best;
 }
@@ -802,6 +814,6 @@ int orc_fit_roll(const float *disp, int W, int H, int u_lo, int v_lo, int u_hi, 
         for (int k = r + 1; k < 3; ++k) s -= A[r][k] * g[k];
         g[r] = s / A[r][r];
     }
-    *roll = atan(-g[1] / g[2]);
+    *roll = atan((MUT(15) ? g[1] : -g[1]) / g[2]);
     return n;
 }
