@@ -95,3 +95,46 @@ def kink_free_alpha(a0, a1, delta, H, h0, h1, step=0.0071):
             return a0
         a0 += step
     raise AssertionError("no kink-free alpha0 found")
+
+
+def near_flat_slack(warped, D, ncc_r, agg_r):
+    """Extra error allowed where a warped-target block is nearly flat.
+
+    A cost of Eq. 3 is a centred dot product over n sigma_l sigma_r.  An
+    intensity error e <= TOL_WARP in the warped block (the bound asserted on
+    the warped image) moves the numerator by at most sqrt(n) sigma_l
+    sqrt(n) e (Cauchy-Schwarz) and sigma_r by at most e, so the cost moves by
+    at most 2 e / sigma_r: large where sigma_r is small but above the flat
+    threshold.  Returns (slack_l, slack_r) of shape [H][W][D] for the two
+    cost volumes and their aggregates (the maximum over the bilateral
+    window, since a weighted mean moves by no more than its largest term).
+    A block whose variance lies within 20 % of the flat threshold may be
+    classed differently by the two sides; there the slack is 2 (any cost)."""
+    from scipy.ndimage import maximum_filter
+    H, W = warped.shape
+    r = ncc_r
+    # block sigma of the warped image at centres x in [-(D-1), W), clamp-to-edge
+    pad = np.pad(warped, ((r, r), (D - 1 + r, r)), mode="edge")
+    n = (2 * r + 1) ** 2
+    s = np.zeros((H, W + D - 1))
+    s2 = np.zeros((H, W + D - 1))
+    for j in range(2 * r + 1):
+        for i in range(2 * r + 1):
+            blk = pad[j:j + H, i:i + W + D - 1]
+            s += blk
+            s2 += blk * blk
+    var = np.maximum(s2 / n - (s / n) ** 2, 0.0)
+    slack = np.where(var > 0, 2.0 * TOL_WARP / np.sqrt(np.maximum(var, 1e-300)), 0.0)
+    slack = np.where(var < 0.8e-6, 0.0, slack)                 # flat on both sides: c = 0
+    slack = np.where(np.abs(var - 1e-6) <= 0.2e-6, 2.0, slack)  # flatness may flip
+    slack = np.minimum(slack, 2.0)
+    u = np.arange(W)[None, :, None]
+    d = np.arange(D)[None, None, :]
+    # cost_l(u, d) pairs the left block at u with the warped block at u - d;
+    # cost_r(u, d) pairs the left block at u + d with the warped block at u
+    sl = slack[:, (u - d + D - 1)[0]]
+    sr = np.broadcast_to(slack[:, D - 1:][:, :, None], (H, W, D))
+    k = 2 * agg_r + 1
+    agg_l = maximum_filter(sl, size=(k, k, 1), mode="nearest")
+    agg_r = maximum_filter(sr, size=(k, k, 1), mode="nearest")
+    return sl, sr, agg_l, agg_r

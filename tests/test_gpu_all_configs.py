@@ -1,0 +1,61 @@
+"""Every compiled parameter set of the FP32 path against the oracle: D in
+{16, 32, 64} x NCC radius 1..5 x bilateral radius 1..7 (105 kernel sets), on
+a small ragged frame; and every radius pair once for the 16-bit volumes.
+Checked: aggregated volumes (TOL_AGG for FP32), labels (mismatches only at
+near-ties), and the subpixel map where well conditioned.  Small ragged
+frames reach nearly flat warped blocks (a dark patch clipped at 0 seen
+through a wide block) far more often than the larger parity scenes; there
+the FP32 cost is ill conditioned and the bound widens by the near-flat slack
+(2 TOL_WARP / sigma_r of the warped block)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from helpers import (DEN_MIN, TAU_TIE, TOL_AGG, TOL_DSUB, near_flat_slack, run_gpu,
+                     run_oracle)
+from paper_1807_07433_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = list(itertools.product((16, 32, 64), range(1, 6), range(1, 8)))
+
+
+def _check(w, vt=0, agg_tol=TOL_AGG):
+    from paper_1807_07433_gb300 import sr
+    left, right, _ = synth.make_pair(w.scene)
+    g = run_gpu(w, left, right, keep_agg=True, vol_dtype=vt,
+                buffers=(("agg_l", sr.SR_BUF_AGG_L), ("agg_r", sr.SR_BUF_AGG_R),
+                         ("dsub", sr.SR_BUF_DSUB)))
+    o = run_oracle(w, left, right,
+                   ("agg_l", "agg_r", "lbl_l", "gap_l", "den_l", "dsub", "warped"))
+    _, _, slack_l, slack_r = near_flat_slack(o.warped, w.D, w.ncc_r, w.agg_r)
+    for side, slack in (("l", slack_l), ("r", slack_r)):
+        err = np.abs(g["agg_" + side].astype(np.float64) - getattr(o, "agg_" + side))
+        over = err > agg_tol + slack
+        assert not over.any(), (side, np.argwhere(over)[:5].tolist(), err[over][:5])
+    if vt == 0:
+        px = slack_l.max(axis=2)                 # worst slack of the pixel
+        diff = g["wta"].astype(np.int64) != o.lbl_l
+        assert not (diff & (o.gap_l >= TAU_TIE + 2 * px)).any()
+        # the parabola's conditioning bound scales with the pixel's slack
+        den_min = DEN_MIN * np.maximum(1.0, px / TOL_AGG)
+        ok = (g["wta"] == o.lbl_l) & (o.gap_l >= TAU_TIE) & \
+            ((np.abs(o.den_l) >= den_min) | (o.den_l == 0))
+        assert ok.mean() > 0.5
+        assert (np.abs(g["dsub"][ok] - o.dsub[ok]) <= TOL_DSUB).all()
+
+
+@pytest.mark.parametrize("D,ncc_r,agg_r", CONFIGS, ids=lambda x: str(x))
+def test_every_fp32_kernel_set(D, ncc_r, agg_r):
+    _check(synth.small(53, 29, D=D, ncc_r=ncc_r, agg_r=agg_r, seed=1000 + D + 10 * ncc_r + agg_r))
+
+
+@pytest.mark.parametrize("vt", [1, 2])
+@pytest.mark.parametrize("ncc_r,agg_r", [(1, 7), (2, 1), (3, 5), (4, 3), (5, 6)])
+def test_16bit_volumes(vt, ncc_r, agg_r):
+    # a stored cost carries up to 2^-11 (FP16) or 2^-8 (BF16) of relative
+    # rounding; the aggregate is a weighted mean of such costs
+    tol = 2e-3 if vt == 1 else 8e-3
+    _check(synth.small(53, 29, D=64, ncc_r=ncc_r, agg_r=agg_r, seed=2000 + 10 * ncc_r + agg_r),
+           vt=vt, agg_tol=tol)
