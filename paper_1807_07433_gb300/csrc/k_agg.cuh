@@ -43,7 +43,13 @@ namespace sr {
 
 constexpr int kAggTX = 32, kAggTY = 4, kAggPX = 8, kAggPix = kAggTX * kAggTY;
 
-template <int R, int D, typename VT>
+// SH: the tile reads a cost row sheared, pixel u at disparity d from column
+// u + d of an extended reference volume (the target view of Sec. II-B-1):
+// the ring slot holds D/16 boxes of 16 disparities x (32 + 2R + 16) pixels
+// of a 2-D tensor map, one box per 16-disparity chunk; odd chunks start one
+// pixel earlier, which moves their words to the other half of the shared-
+// memory banks (the chunk stride is a multiple of 32 words).
+template <int R, int D, typename VT, bool SH = false>
 struct AggCfg {
     static constexpr int SLOTS = D / 2;            // lanes per pixel group
     static constexpr int G = 32 / SLOTS;           // pixel groups per warp
@@ -53,9 +59,14 @@ struct AggCfg {
     static constexpr int WS = 2 * R + 1;           // window side
     static constexpr int TXE = kAggTX + 2 * R;     // ring row width (pixels)
     static constexpr int TYE = kAggTY + 2 * R;     // source rows per tile
-    static constexpr int RING = TXE * D;           // elements of one cost row of the tile
-    // slot stride: RING rounded up to 128 bytes, the alignment a tensor-map
-    // copy needs for its destination
+    static constexpr int NCH = D / 16;             // sheared: 16-disparity chunks
+    static constexpr int BH = TXE + 16;            // sheared: pixels of a chunk's box
+    // sheared: chunk stride, rounded up to 128 bytes (a tensor-map copy's
+    // destination alignment)
+    static constexpr int CSE = (int)(((BH * 16 * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
+    // elements of one cost row of the tile
+    static constexpr int RING = SH ? NCH * CSE : TXE * D;
+    // slot stride: RING rounded up to 128 bytes
     static constexpr int RINGS = (int)(((RING * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
     static constexpr int WRING = kAggTY * WS * kAggTX;  // floats per weight slot
     // weight-ring slots: two let the warps of a CTA compute the next row's
@@ -144,9 +155,9 @@ __device__ __forceinline__ float ex2_approx(float x) {   // 2^x, hardware approx
 }
 
 // Shared-memory carve-up of an aggregation CTA (see AggCfg).
-template <int R, int D, typename VT>
+template <int R, int D, typename VT, bool SH = false>
 struct AggSmem {
-    using C = AggCfg<R, D, VT>;
+    using C = AggCfg<R, D, VT, SH>;
     unsigned char *raw;
     __device__ float *epi() const { return reinterpret_cast<float *>(raw); }
     __device__ VT *ring() const { return reinterpret_cast<VT *>(raw); }
@@ -160,8 +171,8 @@ struct AggSmem {
     __device__ int *start() const { return next_slot() + 4; }
 };
 
-template <int R, int D, typename VT>
-__device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT> &sm) {
+template <int R, int D, typename VT, bool SH>
+__device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT, SH> &sm) {
     if (threadIdx.x == 0) {
         mbar_init(&sm.bars()[0], 1);
         mbar_init(&sm.bars()[1], 1);
@@ -174,13 +185,15 @@ __device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT> &sm) {
 // tile to tile of a persistent CTA.  All threads of the CTA take part.
 //
 // BAND: the ring holds the D = kBandD disparities [dlo, dlo + D) of each pixel,
-// loaded as one 2-D tensor-map box per row (tmap); otherwise the D
-// disparities of the volume, one bulk copy per row.  WIN: win restricts the
-// WTA and Eq. 12 of each pixel to its window (see AggWin); a compile-time
-// choice, so that the full search keeps its own code.
-template <int R, int D, bool GU8, typename VT, bool BAND = false, bool WIN = BAND>
-__device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &ph,
-                                         const VT *__restrict__ vol, const uint8_t *__restrict__ gl,
+// loaded as one 2-D tensor-map box per row (tmap); SH: the sheared row of an
+// extended volume (see AggCfg), D/16 boxes per row (tmap); otherwise the D
+// disparities of the volume (rows of vpitch pixels), one bulk copy per row.
+// WIN: win restricts the WTA and Eq. 12 of each pixel to its window (see
+// AggWin); a compile-time choice, so that the full search keeps its own code.
+template <int R, int D, bool GU8, typename VT, bool BAND = false, bool WIN = BAND, bool SH = false>
+__device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsigned &ph,
+                                         const VT *__restrict__ vol, int vpitch,
+                                         const uint8_t *__restrict__ gl,
                                          int pitch, const float *__restrict__ gf, int W, int H,
                                          float kd, float kr, int16_t *__restrict__ lbl,
                                          float *__restrict__ dsub, float *__restrict__ agg,
@@ -188,7 +201,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
                                          int withhold_last, int x0, int y0,
                                          const void *tmap = nullptr, int dlo = 0,
                                          const AggWin &win = AggWin()) {
-    using C = AggCfg<R, D, VT>;
+    using C = AggCfg<R, D, VT, SH>;
     float *smem = sm.epi();                      // epilogue view
     VT *ring = sm.ring();                        // [2][TXE][D] cost rows
     float *wring = sm.wring();                   // [2][4][WS][32] weights
@@ -219,8 +232,21 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
             tma_load_2d(ring + (j & 1) * C::RINGS, tmap, dlo, y * W + x0 - R, bar);
             return;
         }
+        if (SH) {
+            // chunk c: disparities [16c, 16c + 16) of volume columns
+            // x0 - R + 16c - (c & 1) + [0, BH); tile pixel i at disparity
+            // 16c + m sits in box row i + m + (c & 1).  As for BAND, columns
+            // beyond the row's ends come from the neighbouring rows (or are
+            // zeros) and meet zero weights.
+            mbar_arrive_expect_tx(bar, (unsigned)(C::NCH * C::BH * 16 * sizeof(VT)));
+#pragma unroll
+            for (int c = 0; c < C::NCH; ++c)
+                tma_load_2d(ring + (j & 1) * C::RINGS + c * C::CSE, tmap, 16 * c,
+                            y * vpitch + x0 - R + 16 * c - (c & 1), bar);
+            return;
+        }
         VT *dst = ring + (j & 1) * C::RINGS + (xs - (x0 - R)) * D;
-        const VT *src = vol + ((size_t)y * W + xs) * D;
+        const VT *src = vol + ((size_t)y * vpitch + xs) * D;
         mbar_arrive_expect_tx(bar, row_bytes);
         tma_load_1d(dst, src, row_bytes, bar);
     };
@@ -280,7 +306,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         for (int k = 0; k < NG; ++k)
             if (tid + k * C::NT < C::GUIDE) guide[tid + k * C::NT] = g[k];
     }
-    if (!BAND && (xs > x0 - R || xe < x0 + kAggTX + R)) {
+    if (!BAND && !SH && (xs > x0 - R || xe < x0 + kAggTX + R)) {
         for (int i = tid; i < 2 * C::RINGS; i += C::NT) {
             const int c = (i % C::RINGS) / D + x0 - R;
             if (c < xs || c >= xe) ring[i] = VT(0.0f);
@@ -318,12 +344,22 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
         const int y = y0 - R + j;
         if (y >= 0 && y < H) {
             mbar_wait(bars + (j & 1), (ph >> (j & 1)) & 1u, wait_cycles, err);
-            const VT *rs = ring + (j & 1) * C::RINGS + bx * D + 2 * sl;
             const float *ws = wring + (j % C::WSL) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
+            if (SH) {   // lane sl: disparities sl and sl + SLOTS (see the epilogue)
+                const VT *slot = ring + (j & 1) * C::RINGS + bx * 16;
+                const int da = sl, db = sl + C::SLOTS;
+                const VT *ra = slot + (da >> 4) * C::CSE + ((da & 15) + ((da >> 4) & 1)) * 16 + (da & 15);
+                const VT *rb = slot + (db >> 4) * C::CSE + ((db & 15) + ((db >> 4) & 1)) * 16 + (db & 15);
 #pragma unroll
-            for (int i = 0; i < kAggPX + 2 * R; ++i)
-                cst[i] = load_pair(rs + i * D);
+                for (int i = 0; i < kAggPX + 2 * R; ++i)
+                    cst[i] = make_float2(load_one(ra + i * 16), load_one(rb + i * 16));
+            } else {
+                const VT *rs = ring + (j & 1) * C::RINGS + bx * D + 2 * sl;
+#pragma unroll
+                for (int i = 0; i < kAggPX + 2 * R; ++i)
+                    cst[i] = load_pair(rs + i * D);
+            }
 #pragma unroll
             for (int py = 0; py < kAggTY; ++py) {
                 const int dyi = j - py;
@@ -369,9 +405,9 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT> &sm, unsigned &
     for (int py = 0; py < kAggTY; ++py)
 #pragma unroll
         for (int px = 0; px < kAggPX; ++px) {
-            float *e = E + (grp * 32 + py * kAggPX + px) * (D + 1) + 2 * sl;
-            e[0] = acc[py][px].x;
-            e[1] = acc[py][px].y;
+            float *e = E + (grp * 32 + py * kAggPX + px) * (D + 1);
+            e[SH ? sl : 2 * sl] = acc[py][px].x;
+            e[SH ? sl + C::SLOTS : 2 * sl + 1] = acc[py][px].y;
         }
     __syncthreads();
     for (int pw = lane; pw < 32 * C::G; pw += 32) {
@@ -433,16 +469,34 @@ __global__ void __launch_bounds__(AggCfg<R, D, VT>::NT, AggCfg<R, D, VT>::MINB)
 k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
           const float *__restrict__ gf, int W, int H, float kd, float kr,
           int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
-          int *__restrict__ err, long long wait_cycles, int withhold_last, AggWin win) {
+          int *__restrict__ err, long long wait_cycles, int withhold_last, AggWin win,
+          int vpitch) {
     // restricted search: tiles of the band kernel are not this kernel's
     if (WIN && win.band && win.band[blockIdx.y * gridDim.x + blockIdx.x] >= 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const AggSmem<R, D, VT> sm{smem_raw};
     agg_init_barriers(sm);
     unsigned ph = 0;
-    agg_tile<R, D, GU8, VT, false, WIN>(sm, ph, vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg,
+    agg_tile<R, D, GU8, VT, false, WIN>(sm, ph, vol, vpitch, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg,
                                         err, wait_cycles, withhold_last, blockIdx.x * kAggTX,
                                         blockIdx.y * kAggTY, nullptr, 0, win);
+}
+
+// Target view from the extended reference volume (see AggCfg): the guide is
+// the warped target, no subpixel map.
+template <int R, int D, typename VT>
+__global__ void __launch_bounds__(AggCfg<R, D, VT, true>::NT, AggCfg<R, D, VT, true>::MINB)
+k_agg_shear(const __grid_constant__ CUtensorMap tmap, int vpitch, const float *__restrict__ gf,
+            int W, int H, float kd, float kr, int16_t *__restrict__ lbl, float *__restrict__ agg,
+            int *__restrict__ err, long long wait_cycles, int withhold_last) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const AggSmem<R, D, VT, true> sm{smem_raw};
+    agg_init_barriers(sm);
+    unsigned ph = 0;
+    agg_tile<R, D, false, VT, false, false, true>(sm, ph, nullptr, vpitch, nullptr, 0, gf, W, H,
+                                                  kd, kr, lbl, nullptr, agg, err, wait_cycles,
+                                                  withhold_last, blockIdx.x * kAggTX,
+                                                  blockIdx.y * kAggTY, &tmap);
 }
 
 // Band kernel of the restricted search: the tile's kBandD-disparity slice
@@ -459,7 +513,7 @@ k_agg_band(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__
     const AggSmem<R, kBandD, VT> sm{smem_raw};
     agg_init_barriers(sm);
     unsigned ph = 0;
-    agg_tile<R, kBandD, GU8, VT, true>(sm, ph, nullptr, gl, pitch, gf, W, H, kd, kr, lbl, dsub,
+    agg_tile<R, kBandD, GU8, VT, true>(sm, ph, nullptr, W, gl, pitch, gf, W, H, kd, kr, lbl, dsub,
                                        nullptr, err, wait_cycles, 0, blockIdx.x * kAggTX,
                                        blockIdx.y * kAggTY, &tmap, dlo, win);
 }
@@ -499,7 +553,7 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
         const PairDesc &P = pairs[p];
         const int tl = t - st[p], tx = (P.W + kAggTX - 1) / kAggTX;
         agg_tile<R, D, !TARGET, VT>(sm, ph, static_cast<const VT *>(TARGET ? P.vol_r : P.vol_l),
-                                    TARGET ? nullptr : P.left, P.pitch, TARGET ? P.rw : nullptr,
+                                    P.W, TARGET ? nullptr : P.left, P.pitch, TARGET ? P.rw : nullptr,
                                     P.W, P.H, kd, kr, TARGET ? P.lbl_r : P.lbl_l,
                                     TARGET ? nullptr : P.dsub, nullptr, err, wait_cycles, 0,
                                     (tl % tx) * kAggTX, (tl / tx) * kAggTY);
@@ -509,7 +563,7 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
 template <int R, int D, typename VT, bool WIN>
 cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
-                         const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
+                         const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch) {
     using C = AggCfg<R, D, VT>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
     auto k = gl ? k_agg_wta<R, D, true, VT, WIN> : k_agg_wta<R, D, false, VT, WIN>;
@@ -517,7 +571,22 @@ cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const floa
                                          (int)C::SMEM_SINGLE);
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
-                                    dbg.wait_cycles, dbg.withhold_last, win);
+                                    dbg.wait_cycles, dbg.withhold_last, win, vpitch);
+    return cudaGetLastError();
+}
+
+template <int R, int D, typename VT>
+cudaError_t agg_shear_launch_t(const CUtensorMap &tmap, int vpitch, const float *gf, int W,
+                               int H, float kd, float kr, int16_t *lbl, float *agg,
+                               const AggDebug &dbg, cudaStream_t st) {
+    using C = AggCfg<R, D, VT, true>;
+    const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
+    auto k = k_agg_shear<R, D, VT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM_SINGLE);
+    if (e != cudaSuccess) return e;
+    k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(tmap, vpitch, gf, W, H, kd, kr, lbl, agg, dbg.err,
+                                    dbg.wait_cycles, dbg.withhold_last);
     return cudaGetLastError();
 }
 
@@ -573,9 +642,20 @@ int agg_occ_t() {
 template <int D, typename VT, bool WIN>
 cudaError_t agg_launch_d(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub,
-                         float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
+                         float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win,
+                         int vpitch) {
     SR_AGG_R_SWITCH(agg_r, return (agg_launch_t<R_, D, VT, WIN>(vol, gl, pitch, gf, W, H, kd, kr,
-                                                                lbl, dsub, agg, dbg, st, win)))
+                                                                lbl, dsub, agg, dbg, st, win,
+                                                                vpitch)))
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename VT>
+cudaError_t agg_shear_launch_d(const CUtensorMap &tmap, int vpitch, const float *gf, int W, int H,
+                               int agg_r, float kd, float kr, int16_t *lbl, float *agg,
+                               const AggDebug &dbg, cudaStream_t st) {
+    SR_AGG_R_SWITCH(agg_r, return (agg_shear_launch_t<R_, D, VT>(tmap, vpitch, gf, W, H, kd, kr,
+                                                                 lbl, agg, dbg, st)))
     return cudaErrorInvalidValue;
 }
 

@@ -1,0 +1,10 @@
+// Eqs. 8-12 aggregation/WTA of the target view, read sheared from the
+// extended reference volume, instantiated for D = 64, volumes stored as __nv_bfloat16.
+#include "k_agg.cuh"
+
+namespace sr {
+cudaError_t launch_aggs_d64_bf16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st) {
+    return agg_shear_launch_d<64, __nv_bfloat16>(*static_cast<const CUtensorMap *>(tmap), vpitch, gf, W, H,
+                                       agg_r, kd, kr, lbl, agg, dbg, st);
+}
+}  // namespace sr

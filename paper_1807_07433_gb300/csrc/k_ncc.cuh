@@ -4,7 +4,11 @@
 //   reference volume: c(u,v,d) = NCC(left block at u, warped-target block at u-d)
 //   target volume:    c(u,v,d) = NCC(left block at u+d, warped-target block at u)
 // (the two volumes of Sec. II-B-1; c of the reference volume at (u,v,d) equals
-// c of the target volume at (u-d,v,d)).
+// c of the target volume at (u-d,v,d)).  The reference kernel also runs on
+// an extended output width Wo = W + D - 1: block centres u in [W, W + D - 1)
+// are clamp-to-edge blocks like any other, and that one extended volume
+// holds both (target c(u,v,d) = extended reference c(u+d,v,d)); entries with
+// u - d >= W are computed from clamped statistics and never read.
 //
 // Numerics.  The numerator of Eq. 3, sum(i_l i_r) - n mu_l mu_r, equals
 // sum((f - mu_f) * (s - K)) for ANY constant K when f is the block that stays
@@ -59,7 +63,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
                                          const float *__restrict__ inv_l,
                                          const float *__restrict__ mu_r,
                                          const float *__restrict__ inv_r, int W, int H,
-                                         VT *__restrict__ vol, int x0, int y0,
+                                         VT *__restrict__ vol, int Wo, int x0, int y0,
                                          int dlo = 0, int dhi = D - 1) {
     using S = NccSmem<RN, D>;
     constexpr int B = S::B, FW = S::FW, SW = S::SW, TH = S::TH, XW = S::XW;
@@ -71,7 +75,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     // overlaps the staging below.
     const int tx = tid % kNccTX, ty = tid / kNccTX;
     const int u = x0 + tx, v = y0 + ty;
-    const bool inside = u < W && v < H;
+    const bool inside = u < Wo && v < H;
     const size_t rowo = (size_t)(inside ? v : 0) * WE;
     const int uc = inside ? u : 0;
     const float m = TARGET ? mu_r[rowo + uc + D - 1] : mu_l[rowo + uc];
@@ -129,7 +133,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     // n/(n sigma_f) of the fixed block (Eq. 3 divides n*cov by n*sigma_f*sigma_s).
     constexpr float n = (float)(B * B);
     const float inv_f = n * inv_f0;
-    VT *out = vol + ((size_t)v * W + u) * D;
+    VT *out = vol + ((size_t)v * Wo + u) * D;
 
 #pragma unroll 1
     for (int d0 = 0; d0 < D; d0 += DC) {
@@ -165,6 +169,10 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
             const int so = TARGET ? d : -d;
             const float num = fmaf(-sa, mu_s_row[so] - kNccOffset, acc[i]);
             cst[i] = num * inv_f * inv_s_row[so];
+            // extended volume: a sliding centre u - d >= W has no statistics
+            // of its own; no cost is taken from there, but readers meet the
+            // entry with weight zero, so it is stored as 0 (finite)
+            if (!TARGET && u - d >= W) cst[i] = 0.0f;
         }
 #pragma unroll
         for (int i = 0; i < DC; i += 8) store8(out + d0 + i, cst + i);
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(kNccThreads)
 k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
       const float *__restrict__ mu_l, const float *__restrict__ inv_l,
       const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
-      VT *__restrict__ vol, const int2 *__restrict__ range) {
+      VT *__restrict__ vol, int Wo, const int2 *__restrict__ range) {
     __shared__ NccSmem<RN, D> sm;
     int dlo = 0, dhi = D - 1;
     if (range) {   // restricted search: the disparities the tile's readers need
@@ -184,7 +192,7 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
         dlo = r.x;
         dhi = r.y;
     }
-    ncc_tile<RN, D, TARGET, VT>(sm, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol,
+    ncc_tile<RN, D, TARGET, VT>(sm, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, Wo,
                                 blockIdx.x * kNccTX, blockIdx.y * kNccTY, dlo, dhi);
 }
 
@@ -211,7 +219,7 @@ k_ncc_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
         const PairDesc &P = pairs[p];
         const int tl = t - st[p], tx = (P.W + kNccTX - 1) / kNccTX;
         ncc_tile<RN, D, TARGET, VT>(sm, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r,
-                                    P.W, P.H, static_cast<VT *>(TARGET ? P.vol_r : P.vol_l),
+                                    P.W, P.H, static_cast<VT *>(TARGET ? P.vol_r : P.vol_l), P.W,
                                     (tl % tx) * kNccTX, (tl / tx) * kNccTY);
         if (!next) t += gridDim.x;
     }
@@ -220,13 +228,13 @@ k_ncc_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
 template <int RN, int D, typename VT>
 cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
-                         const float *inv_r, int W, int H, VT *vol, cudaStream_t st,
+                         const float *inv_r, int W, int H, VT *vol, int Wo, cudaStream_t st,
                          const int2 *range) {
-    const dim3 grid((W + kNccTX - 1) / kNccTX, (H + kNccTY - 1) / kNccTY);
+    const dim3 grid((Wo + kNccTX - 1) / kNccTX, (H + kNccTY - 1) / kNccTY);
     if (target)
-        k_ncc<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, range);
+        k_ncc<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, Wo, range);
     else
-        k_ncc<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, range);
+        k_ncc<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, Wo, range);
     return cudaGetLastError();
 }
 
@@ -260,10 +268,10 @@ int ncc_occ_t() {
 template <int D, typename VT>
 cudaError_t ncc_launch_d(bool target, const uint8_t *left, int pitch, const float *rw,
                          const float *mu_l, const float *inv_l, const float *mu_r,
-                         const float *inv_r, int W, int H, int ncc_r, VT *vol,
+                         const float *inv_r, int W, int H, int ncc_r, VT *vol, int Wo,
                          cudaStream_t st, const int2 *range) {
     SR_NCC_RN_SWITCH(ncc_r, return (ncc_launch_t<RN_, D, VT>(target, left, pitch, rw, mu_l, inv_l,
-                                                             mu_r, inv_r, W, H, vol, st, range)))
+                                                             mu_r, inv_r, W, H, vol, Wo, st, range)))
     return cudaErrorInvalidValue;
 }
 

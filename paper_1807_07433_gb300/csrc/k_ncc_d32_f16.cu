@@ -2,9 +2,9 @@
 #include "k_ncc.cuh"
 
 namespace sr {
-cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range) {
+cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range) {
     return ncc_launch_d<32, __half>(target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r,
-                                   static_cast<__half *>(vol), st, range);
+                                   static_cast<__half *>(vol), Wo, st, range);
 }
 cudaError_t launch_ncc_batch_d32_f16(bool target, const PairDesc *pairs, const int *start, int n,
                                   int ncc_r, int grid, int *next, cudaStream_t st) {

@@ -13,34 +13,43 @@
 #include "sr_ctx.cuh"
 
 namespace sr {
-cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d16_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d16_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d32_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d64_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, cudaStream_t st, const int2 *range);
-cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_ncc_d16_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d16_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d16_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d32_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d32_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d32_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d64_f32(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d64_f16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_ncc_d64_bf16(bool target, const uint8_t *left, int pitch, const float *rw, const float *mu_l, const float *inv_l, const float *mu_r, const float *inv_r, int W, int H, int ncc_r, void *vol, int Wo, cudaStream_t st, const int2 *range);
+cudaError_t launch_agg_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
 
-cudaError_t launch_aggw_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
-cudaError_t launch_aggw_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win);
+cudaError_t launch_aggw_d16_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d16_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d16_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d32_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d32_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d32_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d64_f32(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d64_f16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggw_d64_bf16(const void *vol, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, float *agg, const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch);
+cudaError_t launch_aggs_d16_f32(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d16_f16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d16_bf16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d32_f32(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d32_f16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d32_bf16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d64_f32(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d64_f16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+cudaError_t launch_aggs_d64_bf16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
 cudaError_t launch_agg_band_f32(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 cudaError_t launch_agg_band_f16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 cudaError_t launch_agg_band_bf16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
@@ -100,11 +109,13 @@ bool agg_supported(int D, int agg_r) {
 cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
                        const float *mu_l, const float *inv_l, const float *mu_r,
                        const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
-                       cudaStream_t st, const int2 *range) {
+                       cudaStream_t st, const int2 *range, int Wo) {
+    if (Wo <= 0) Wo = W;
+    if (target && Wo != W) return cudaErrorInvalidValue;
     switch (D) {
-        case 16: SR_VT_DISPATCH(launch_ncc, 16, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st, range)
-        case 32: SR_VT_DISPATCH(launch_ncc, 32, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st, range)
-        case 64: SR_VT_DISPATCH(launch_ncc, 64, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, st, range)
+        case 16: SR_VT_DISPATCH(launch_ncc, 16, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, Wo, st, range)
+        case 32: SR_VT_DISPATCH(launch_ncc, 32, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, Wo, st, range)
+        case 64: SR_VT_DISPATCH(launch_ncc, 64, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, Wo, st, range)
         default: return cudaErrorInvalidValue;
     }
 }
@@ -112,21 +123,36 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
 cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
-                       const AggDebug &dbg, cudaStream_t st, const AggWin &win) {
+                       const AggDebug &dbg, cudaStream_t st, const AggWin &win, int vpitch) {
     const float log2e = 1.4426950408889634f;
     const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
+    if (vpitch <= 0) vpitch = W;
     if (win.radius >= 0) {   // restricted search: the windowed kernels
         switch (D) {
-            case 16: SR_VT_DISPATCH(launch_aggw, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
-            case 32: SR_VT_DISPATCH(launch_aggw, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
-            case 64: SR_VT_DISPATCH(launch_aggw, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+            case 16: SR_VT_DISPATCH(launch_aggw, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win, vpitch)
+            case 32: SR_VT_DISPATCH(launch_aggw, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win, vpitch)
+            case 64: SR_VT_DISPATCH(launch_aggw, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win, vpitch)
             default: return cudaErrorInvalidValue;
         }
     }
     switch (D) {
-        case 16: SR_VT_DISPATCH(launch_agg, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
-        case 32: SR_VT_DISPATCH(launch_agg, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
-        case 64: SR_VT_DISPATCH(launch_agg, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win)
+        case 16: SR_VT_DISPATCH(launch_agg, 16, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win, vpitch)
+        case 32: SR_VT_DISPATCH(launch_agg, 32, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win, vpitch)
+        case 64: SR_VT_DISPATCH(launch_agg, 64, vt, vol, guide_u8, pitch, guide_f32, W, H, agg_r, kd, kr, lbl, dsub, agg, dbg, st, win, vpitch)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_agg_shear(const void *tmap, int vt, const float *guide_f32, int W, int H,
+                             int D, int agg_r, float gamma_d, float gamma_r, int16_t *lbl,
+                             float *agg, const AggDebug &dbg, cudaStream_t st) {
+    const float log2e = 1.4426950408889634f;
+    const float kd = log2e / (gamma_d * gamma_d), kr = log2e / (gamma_r * gamma_r);
+    const int vpitch = W + D - 1;
+    switch (D) {
+        case 16: SR_VT_DISPATCH(launch_aggs, 16, vt, tmap, vpitch, guide_f32, W, H, agg_r, kd, kr, lbl, agg, dbg, st)
+        case 32: SR_VT_DISPATCH(launch_aggs, 32, vt, tmap, vpitch, guide_f32, W, H, agg_r, kd, kr, lbl, agg, dbg, st)
+        case 64: SR_VT_DISPATCH(launch_aggs, 64, vt, tmap, vpitch, guide_f32, W, H, agg_r, kd, kr, lbl, agg, dbg, st)
         default: return cudaErrorInvalidValue;
     }
 }
@@ -198,7 +224,7 @@ int agg_batch_occupancy(int D, int agg_r, int vt) {
 
 namespace {
 
-const char *const kStageNames = "prep,ncc_ref,ncc_tgt,agg_ref,agg_tgt,lrc_post";
+const char *const kStageNames = "prep,ncc,agg_ref,agg_tgt,lrc_post";
 
 }  // namespace
 
@@ -262,6 +288,28 @@ bool encode_volume_map(CUtensorMap *m, void *vol, int vt, int W, int H, int D, i
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// Tensor map of the extended reference volume [H][W+D-1][D] viewed as
+// [H*(W+D-1)][D], box 16 disparities x (32 + 2 agg_r + 16) pixels, zeros
+// outside (see launch_agg_shear).
+bool sr::encode_shear_map(void *tmap, const void *volx, int vt, int W, int H, int D, int agg_r) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = vt == sr::kVolF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : vt == sr::kVolF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)(W + D - 1) * H};
+    const cuuint64_t strides[1] = {(cuuint64_t)D * sr::vol_elem_bytes(vt)};
+    const cuuint32_t box[2] = {16, (cuuint32_t)(32 + 2 * agg_r + 16)};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(static_cast<CUtensorMap *>(tmap), dt, 2, const_cast<void *>(volx), dims, strides,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
 // IEEE 754 binary16 bit pattern -> float (sign, 5-bit exponent, 10-bit fraction).
 float half_bits_to_float(uint16_t h) {
     const int s = h >> 15, e = (h >> 10) & 0x1f, m = h & 0x3ff;
@@ -304,7 +352,7 @@ const char *sr_stage_names(void) { return kStageNames; }
 
 int sr_kernels_per_match(const sr_ctx *c) {
     (void)c;
-    return 6;   // prep (warp + statistics), 2x ncc, 2x agg, lrc_post
+    return 5;   // prep (warp + statistics), ncc (extended volume), 2x agg, lrc_post
 }
 
 sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
@@ -334,8 +382,10 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
     if (e == cudaSuccess) e = dalloc(&c->mu_r, H * WE);
     if (e == cudaSuccess) e = dalloc(&c->inv_l, H * WE);
     if (e == cudaSuccess) e = dalloc(&c->inv_r, H * WE);
+    // vol_l: the extended reference volume [H][W+D-1][D] of sr_match, or the
+    // reference volume [H][W][D] of sr_match_restricted (a prefix of it)
     const size_t vbytes = npx * D * sr::vol_elem_bytes(p.vol_dtype);
-    if (e == cudaSuccess) e = cudaMalloc(&c->vol_l, vbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->vol_l, H * WE * D * sr::vol_elem_bytes(p.vol_dtype));
     if (e == cudaSuccess) e = cudaMalloc(&c->vol_r, vbytes);
     if (e == cudaSuccess) e = dalloc(&c->dsub, npx);
     if (e == cudaSuccess) e = dalloc(&c->lbl_l, npx);
@@ -430,27 +480,35 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     };
     c->matched = false;
     c->timed = false;
+    if (!c->tmap_x_ok) {
+        if (!sr::encode_shear_map(&c->tmap_x, c->vol_l, p.vol_dtype, W, H, D, p.agg_radius)) {
+            snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed or is unavailable");
+            return SR_ERR_CUDA;
+        }
+        c->tmap_x_ok = true;
+    }
+    const int WE = W + D - 1;
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
                               c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
            "prep");
     SR_TRY(c, mark(), "cudaEventRecord");
+    // one extended reference volume holds both views (target c(u,d) =
+    // extended reference c(u+d,d))
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st),
-           "ncc_ref");
-    SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_ncc(true, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_r, p.vol_dtype, st),
-           "ncc_tgt");
+                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st, nullptr,
+                             WE),
+           "ncc");
     SR_TRY(c, mark(), "cudaEventRecord");
     const sr::AggDebug dbg = agg_debug(c);
     SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
                              p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
-                             dbg, st),
+                             dbg, st, sr::AggWin(), WE),
            "agg_ref");
     SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_agg(c->vol_r, p.vol_dtype, nullptr, 0, c->rw, W, H, D, p.agg_radius, p.gamma_d,
-                             p.gamma_r, c->lbl_r, nullptr, keep ? c->agg_r : nullptr, dbg, st),
+    SR_TRY(c, sr::launch_agg_shear(&c->tmap_x, p.vol_dtype, c->rw, W, H, D, p.agg_radius,
+                                   p.gamma_d, p.gamma_r, c->lbl_r, keep ? c->agg_r : nullptr, dbg,
+                                   st),
            "agg_tgt");
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->alpha0, c->alpha1,
@@ -458,6 +516,7 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
            "lrc_post");
     SR_TRY(c, mark(), "cudaEventRecord");
     c->matched = true;
+    c->vol_ext = true;
     c->agg_valid = keep;
     c->timed = prof;
     return SR_OK;
@@ -539,6 +598,7 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
                                   c->delta, p.lr_thresh, d_disp, d_wta_or_null, st),
            "lrc_post");
     c->matched = true;
+    c->vol_ext = false;
     c->agg_valid = false;
     return SR_OK;
 }
@@ -742,26 +802,42 @@ sr_status sr_get_buffer(sr_ctx *c, sr_buffer which, void *dst, size_t *bytes_ino
             const size_t n = npx * D;
             if (*bytes_inout < n * 4) { *bytes_inout = n * 4; return SR_ERR_INVALID_ARG; }
             if (!c->matched) return SR_ERR_STATE;
-            const void *v = which == SR_BUF_COST_L ? c->vol_l : c->vol_r;
+            // After sr_match both views live in the extended reference volume
+            // (row pitch W + D - 1; the target cost (u, d) is its column
+            // u + d); after sr_match_restricted each view has its own volume.
+            const bool ext = c->vol_ext;
+            const size_t W = c->p.width, H = c->p.height, pitch = ext ? W + D - 1 : W;
+            const bool tgt = which == SR_BUF_COST_R;
+            const void *v = (ext || !tgt) ? c->vol_l : c->vol_r;
+            const size_t m = H * pitch * D;   // elements of the source volume
             SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
-            if (c->p.vol_dtype == SR_VOL_F32) {
-                SR_TRY(c, cudaMemcpy(dst, v, n * 4, cudaMemcpyDefault), "cudaMemcpy");
-            } else {
-                // widen the 16-bit volume to float on the host
-                uint16_t *raw = (uint16_t *)malloc(n * 2);
-                float *wide = (float *)malloc(n * 4);
-                if (!raw || !wide) { free(raw); free(wide); return SR_ERR_OOM; }
-                cudaError_t e = cudaMemcpy(raw, v, n * 2, cudaMemcpyDeviceToHost);
-                if (e == cudaSuccess) {
-                    for (size_t i = 0; i < n; ++i)
-                        wide[i] = c->p.vol_dtype == SR_VOL_F16 ? half_bits_to_float(raw[i])
-                                                               : bf16_bits_to_float(raw[i]);
-                    e = cudaMemcpy(dst, wide, n * 4, cudaMemcpyDefault);
-                }
-                free(raw);
-                free(wide);
-                if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(volume)");
+            // the source widened to float on the host, then the view's elements
+            float *wide = (float *)malloc(m * 4);
+            float *view = ext ? (float *)malloc(n * 4) : wide;
+            uint16_t *raw = c->p.vol_dtype == SR_VOL_F32 ? nullptr : (uint16_t *)malloc(m * 2);
+            if (!wide || !view || (c->p.vol_dtype != SR_VOL_F32 && !raw)) {
+                free(wide); if (ext) free(view); free(raw);
+                return SR_ERR_OOM;
             }
+            cudaError_t e;
+            if (raw) {
+                e = cudaMemcpy(raw, v, m * 2, cudaMemcpyDeviceToHost);
+                for (size_t i = 0; e == cudaSuccess && i < m; ++i)
+                    wide[i] = c->p.vol_dtype == SR_VOL_F16 ? half_bits_to_float(raw[i])
+                                                           : bf16_bits_to_float(raw[i]);
+            } else {
+                e = cudaMemcpy(wide, v, m * 4, cudaMemcpyDeviceToHost);
+            }
+            if (e == cudaSuccess && ext)
+                for (size_t y = 0; y < H; ++y)
+                    for (size_t u = 0; u < W; ++u)
+                        for (size_t d = 0; d < (size_t)D; ++d)
+                            view[(y * W + u) * D + d] = wide[(y * pitch + u + (tgt ? d : 0)) * D + d];
+            if (e == cudaSuccess) e = cudaMemcpy(dst, view, n * 4, cudaMemcpyDefault);
+            free(wide);
+            if (ext) free(view);
+            free(raw);
+            if (e != cudaSuccess) return fail_cuda(c, e, "cudaMemcpy(volume)");
             *bytes_inout = n * 4;
             return take_device_error(c);
         }

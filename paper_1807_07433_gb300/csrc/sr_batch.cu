@@ -78,6 +78,7 @@ struct SrBatch {
     std::vector<int> tiles_pix, tiles_stat, tiles_t4;     // staged order
     std::vector<long long> graph_sizes;                   // size sequence the graph was built for
     std::vector<sr::PairDesc> graph_desc;                 // descriptors a schedule-C graph holds
+    std::vector<CUtensorMap> tmaps;                       // sheared view of each pair's vol_l
     bool tune = false;
     std::string cache_path;
     std::map<std::string, int> tuned;
@@ -115,8 +116,10 @@ namespace {
 size_t pair_scratch_bytes(const sr_params &p, int W, int H) {
     const size_t npx = (size_t)W * H, WE = (size_t)W + p.max_disp - 1;
     const size_t e = sr::vol_elem_bytes(p.vol_dtype);
-    return 2 * a256(npx * 4) + 4 * a256((size_t)H * WE * 4) + 2 * a256(npx * p.max_disp * e) +
-           2 * a256(npx * 2);
+    // vol_l holds the extended reference volume [H][WE][D] (schedule C) or the
+    // reference volume [H][W][D] (persistent schedules, a prefix of it)
+    return 2 * a256(npx * 4) + 4 * a256((size_t)H * WE * 4) + a256((size_t)H * WE * p.max_disp * e) +
+           a256(npx * p.max_disp * e) + 2 * a256(npx * 2);
 }
 
 std::string tune_key(const sr_ctx *c, int n, const sr_pair_desc *pairs) {
@@ -219,15 +222,15 @@ cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     cudaError_t e;
     if ((e = sr::launch_prep(P.left, P.right, P.pitch, P.W, P.H, D, p.ncc_radius, P.alpha0,
                              P.alpha1, P.delta, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, st)) != cudaSuccess) return e;
+    // one extended reference volume for both views, as in sr_match
+    const int WE = P.W + D - 1;
     if ((e = sr::launch_ncc(false, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
-                            P.H, D, p.ncc_radius, P.vol_l, p.vol_dtype, st)) != cudaSuccess) return e;
-    if ((e = sr::launch_ncc(true, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
-                            P.H, D, p.ncc_radius, P.vol_r, p.vol_dtype, st)) != cudaSuccess) return e;
+                            P.H, D, p.ncc_radius, P.vol_l, p.vol_dtype, st, nullptr, WE)) != cudaSuccess) return e;
     if ((e = sr::launch_agg(P.vol_l, p.vol_dtype, P.left, P.pitch, nullptr, P.W, P.H, D,
                             p.agg_radius, p.gamma_d, p.gamma_r, P.lbl_l, P.dsub, nullptr, dbg,
-                            st)) != cudaSuccess) return e;
-    if ((e = sr::launch_agg(P.vol_r, p.vol_dtype, nullptr, 0, P.rw, P.W, P.H, D, p.agg_radius,
-                            p.gamma_d, p.gamma_r, P.lbl_r, nullptr, nullptr, dbg, st)) != cudaSuccess) return e;
+                            st, sr::AggWin(), WE)) != cudaSuccess) return e;
+    if ((e = sr::launch_agg_shear(&b->tmaps[k], p.vol_dtype, P.rw, P.W, P.H, D, p.agg_radius,
+                                  p.gamma_d, p.gamma_r, P.lbl_r, nullptr, dbg, st)) != cudaSuccess) return e;
     return sr::launch_lrc_post(P.lbl_l, P.lbl_r, P.dsub, P.W, P.H, P.alpha0, P.alpha1, P.delta,
                                p.lr_thresh, P.disp, P.wta, st);
 }
@@ -296,6 +299,7 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
     b->tiles_pix.resize(n);
     b->tiles_stat.resize(n);
     b->tiles_t4.resize(n);
+    b->tmaps.resize(n);
     for (int k = 0; k < n; ++k) {
         const sr_pair_desc &in = pairs[order[k]];
         const int W = in.width, H = in.height;
@@ -312,10 +316,12 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
         o.inv_l = reinterpret_cast<float *>(take((size_t)H * WE * 4));
         o.mu_r = reinterpret_cast<float *>(take((size_t)H * WE * 4));
         o.inv_r = reinterpret_cast<float *>(take((size_t)H * WE * 4));
-        o.vol_l = take(npx * D * sr::vol_elem_bytes(p.vol_dtype));
+        o.vol_l = take((size_t)H * WE * D * sr::vol_elem_bytes(p.vol_dtype));
         o.vol_r = take(npx * D * sr::vol_elem_bytes(p.vol_dtype));
         o.lbl_l = reinterpret_cast<int16_t *>(take(npx * 2));
         o.lbl_r = reinterpret_cast<int16_t *>(take(npx * 2));
+        if (!sr::encode_shear_map(&b->tmaps[k], o.vol_l, p.vol_dtype, W, H, D, p.agg_radius))
+            return cudaErrorNotSupported;
         b->tiles_pix[k] = sr::ceil_div(W, sr::kPixTX) * sr::ceil_div(H, sr::kPixTY);
         b->tiles_stat[k] = sr::ceil_div(W + D - 1, sr::kPixTX) * sr::ceil_div(H, sr::kPixTY);
         b->tiles_t4[k] = sr::ceil_div(W, 32) * sr::ceil_div(H, 4);

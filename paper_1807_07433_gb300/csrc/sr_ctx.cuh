@@ -7,7 +7,7 @@
 #include "../../include/sr.h"
 #include "sr_internal.cuh"
 
-constexpr int kStages = 6;    // stages of one sr_match with profiling events
+constexpr int kStages = 5;    // stages of one sr_match with profiling events
 
 struct SrBatch;               // batched-form state, defined in sr_batch.cu
 void sr_batch_free(sr_ctx *c);
@@ -21,7 +21,14 @@ struct sr_ctx {
     bool camera = false;
     // scratch (owned)
     float *rw = nullptr, *mu_l = nullptr, *inv_l = nullptr, *mu_r = nullptr, *inv_r = nullptr;
-    void *vol_l = nullptr, *vol_r = nullptr;   // cost volumes, element type p.vol_dtype
+    // cost volumes, element type p.vol_dtype: vol_l holds the extended
+    // reference volume of sr_match (both views, row pitch W + D - 1) or the
+    // reference volume of sr_match_restricted (pitch W), vol_r the target
+    // volume of sr_match_restricted
+    void *vol_l = nullptr, *vol_r = nullptr;
+    bool vol_ext = false;            // the last match left the extended layout
+    CUtensorMap tmap_x{};            // sheared view of vol_l (launch_agg_shear)
+    bool tmap_x_ok = false;
     float *dsub = nullptr;
     int16_t *lbl_l = nullptr, *lbl_r = nullptr;
     float *agg_l = nullptr, *agg_r = nullptr;

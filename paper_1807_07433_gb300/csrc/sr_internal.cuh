@@ -30,6 +30,10 @@ __device__ __forceinline__ float2 load_pair(const __half *p) {
 __device__ __forceinline__ float2 load_pair(const __nv_bfloat16 *p) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
 }
+// One stored cost, widened to FP32.
+__device__ __forceinline__ float load_one(const float *p) { return *p; }
+__device__ __forceinline__ float load_one(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float load_one(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void store8(float *p, const float *v) {
     reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
     reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
@@ -71,16 +75,19 @@ cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, in
                         int ncc_r, double alpha0, double alpha1, double delta, float *rw,
                         float *mu_l, float *inv_l, float *mu_r, float *inv_r, cudaStream_t st);
 
-// Eq. 3 cost volume [H][W][D], stored as vt (VolType; FP32 arithmetic,
+// Eq. 3 cost volume [H][Wo][D], stored as vt (VolType; FP32 arithmetic,
 // rounded to nearest on store).  target = false: reference volume
 // c(u,v,d) = NCC(left block u, warped-target block u-d); target = true:
 // target volume c(u,v,d) = NCC(left block u+d, warped-target block u).
 //   range (nullable): per 32 x 4 tile, the disparities {lo, hi} that some
 //   reader of the tile needs; chunks of disparities outside are not computed
+//   Wo: output columns, W (0) or, for the reference volume only, the
+//   extended W + D - 1, which holds the target volume too: target
+//   c(u,v,d) = extended c(u+d,v,d) (entries with u - d >= W are not used)
 cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float *rw,
                        const float *mu_l, const float *inv_l, const float *mu_r,
                        const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
-                       cudaStream_t st, const int2 *range = nullptr);
+                       cudaStream_t st, const int2 *range = nullptr, int Wo = 0);
 
 // Bounded-wait settings of the aggregation kernel.  err (nullable) receives 1
 // when a wait for a cost-row copy runs out after wait_cycles SM clocks;
@@ -112,11 +119,26 @@ constexpr int kAggTileX = 32, kAggTileY = 4;   // aggregation tile (pixels)
 // reference view, the Eq. 12 parabola.  Guide: the left image (uint8, when
 // guide_u8 != nullptr) or the warped target (float).  Writes lbl [H][W]
 // int16, dsub [H][W] float (nullable) and, for inspection, the normalised
-// aggregated volume agg [H][W][D] (nullable).
+// aggregated volume agg [H][W][D] (nullable).  vpitch: pixels per row of
+// the volume (0: W; W + D - 1 for the extended reference volume).
 cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
-                       const AggDebug &dbg, cudaStream_t st, const AggWin &win = AggWin());
+                       const AggDebug &dbg, cudaStream_t st, const AggWin &win = AggWin(),
+                       int vpitch = 0);
+
+// The target view's aggregation read from the extended reference volume
+// (launch_ncc with Wo = W + D - 1): pixel u at disparity d takes column
+// u + d, through the 2-D tensor map tmap of encode_shear_map.  Guide: the
+// warped target.  Writes lbl [H][W] and, for inspection, agg (nullable).
+cudaError_t launch_agg_shear(const void *tmap, int vt, const float *guide_f32, int W, int H,
+                             int D, int agg_r, float gamma_d, float gamma_r, int16_t *lbl,
+                             float *agg, const AggDebug &dbg, cudaStream_t st);
+// The tensor map launch_agg_shear reads: the extended volume volx
+// [H][W+D-1][D] viewed as [H*(W+D-1)][D], box 16 disparities x
+// (32 + 2 agg_r + 16) pixels, zeros outside.  tmap: 64-byte aligned storage
+// of a CUtensorMap (128 bytes).  False when the driver refuses the map.
+bool encode_shear_map(void *tmap, const void *volx, int vt, int W, int H, int D, int agg_r);
 
 // The band kernel of the restricted search: tiles with band >= 0 aggregate
 // the kBandD disparities [band, band + kBandD) of their pixels, read through

@@ -22,6 +22,7 @@
 // it needs to start at zero: each stage writes every element that a later
 // stage reads.  Calls whose work overlaps on the GPU (different streams, or
 // different host threads without ordering) race on the array.
+#include <cuda.h>
 #include <math.h>
 
 #include <mutex>
@@ -82,9 +83,9 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     const size_t W = p.width, H = p.height, D = p.max_disp, npx = W * H, WE = W + D - 1;
     const size_t b_img = align256(npx * sizeof(float));
     const size_t b_ext = align256(H * WE * sizeof(float));
-    const size_t b_vol = align256(npx * D * sr::vol_elem_bytes(p.vol_dtype));
+    const size_t b_vol = align256(H * WE * D * sr::vol_elem_bytes(p.vol_dtype));   // extended
     const size_t b_lbl = align256(npx * sizeof(int16_t));
-    const size_t need = 2 * b_img + 4 * b_ext + 2 * b_vol + 2 * b_lbl;
+    const size_t need = 2 * b_img + 4 * b_ext + b_vol + 2 * b_lbl;
     if (need > kSrNoallocScratchBytes) return SR_ERR_UNSUPPORTED;   // frame too large
 
     void *base = nullptr;
@@ -97,24 +98,25 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     float *inv_l = reinterpret_cast<float *>(take(b_ext));
     float *mu_r = reinterpret_cast<float *>(take(b_ext));
     float *inv_r = reinterpret_cast<float *>(take(b_ext));
-    void *vol_l = take(b_vol);
-    void *vol_r = take(b_vol);
+    void *volx = take(b_vol);
     int16_t *lbl_l = reinterpret_cast<int16_t *>(take(b_lbl));
     int16_t *lbl_r = reinterpret_cast<int16_t *>(take(b_lbl));
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const sr::AggDebug dbg;   // default bounded waits; no error word to report through
-    const int Wi = p.width, Hi = p.height, Di = p.max_disp;
+    const int Wi = p.width, Hi = p.height, Di = p.max_disp, WEi = Wi + Di - 1;
+    // the sheared view of the extended volume (a host-side descriptor)
+    CUtensorMap tmap;
+    if (!sr::encode_shear_map(&tmap, volx, p.vol_dtype, Wi, Hi, Di, p.agg_radius))
+        return SR_ERR_CUDA;
     if (sr::launch_prep(d_left, d_right, pitch_bytes, Wi, Hi, Di, p.ncc_radius, alpha0, alpha1,
                         delta, rw, mu_l, inv_l, mu_r, inv_r, st) != cudaSuccess ||
         sr::launch_ncc(false, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
-                       p.ncc_radius, vol_l, p.vol_dtype, st) != cudaSuccess ||
-        sr::launch_ncc(true, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
-                       p.ncc_radius, vol_r, p.vol_dtype, st) != cudaSuccess ||
-        sr::launch_agg(vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius, p.gamma_d,
-                       p.gamma_r, lbl_l, dsub, nullptr, dbg, st) != cudaSuccess ||
-        sr::launch_agg(vol_r, p.vol_dtype, nullptr, 0, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d, p.gamma_r,
-                       lbl_r, nullptr, nullptr, dbg, st) != cudaSuccess ||
+                       p.ncc_radius, volx, p.vol_dtype, st, nullptr, WEi) != cudaSuccess ||
+        sr::launch_agg(volx, p.vol_dtype, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius, p.gamma_d,
+                       p.gamma_r, lbl_l, dsub, nullptr, dbg, st, sr::AggWin(), WEi) != cudaSuccess ||
+        sr::launch_agg_shear(&tmap, p.vol_dtype, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d,
+                             p.gamma_r, lbl_r, nullptr, dbg, st) != cudaSuccess ||
         sr::launch_lrc_post(lbl_l, lbl_r, dsub, Wi, Hi, alpha0, alpha1, delta, p.lr_thresh,
                             d_disp, d_wta_or_null, st) != cudaSuccess)
         return SR_ERR_CUDA;
