@@ -87,7 +87,7 @@ typedef struct sr_ctx sr_ctx;   /* opaque; owns only its device scratch */
 /* Create a context on the current device.  cuda_stream is the cudaStream_t
  * all work is queued on (NULL = legacy default stream).  Allocates the
  * context's scratch: warped image, block statistics, the two cost volumes
- * and the per-pixel maps (about W*H*(2*D*e + 40) bytes, e = 4 bytes per
+ * and the per-pixel maps (about ((2*W + D)*H*D*e + 40*W*H) bytes, e = 4 bytes per
  * stored cost for SR_VOL_F32 and 2 for SR_VOL_F16 / SR_VOL_BF16).
  * Errors: SR_ERR_INVALID_ARG (null out, non-positive sizes or constants),
  * SR_ERR_UNSUPPORTED (D, radii outside the supported set), SR_ERR_OOM,
@@ -115,8 +115,12 @@ sr_status sr_set_camera(sr_ctx *ctx, double f_px, double baseline, double u0, do
  *                    left pixel, NaN where the L-R check (Eq. 11) fails.
  *   d_wta_or_null    optional W x H int16 (dense): the integer WTA residual
  *                    disparity l_ref of the reference view.
- * Asynchronous on the context's stream.  Errors: SR_ERR_INVALID_ARG for
- * null images/output or pitch < W, SR_ERR_CUDA for a failed launch. */
+ * The NCC cost (Eq. 3) is computed once, as the reference volume over
+ * W + D - 1 columns; the target view of Sec. II-B-1 reads it at column
+ * u + d.  Five kernels: prep, ncc, agg_ref, agg_tgt, lrc_post.  The first
+ * call builds the tensor map of that read.  Asynchronous on the context's
+ * stream.  Errors: SR_ERR_INVALID_ARG for null images/output or pitch < W,
+ * SR_ERR_CUDA for a failed launch or a driver that refuses the tensor map. */
 sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                    float *d_disp, int16_t *d_wta_or_null);
 
@@ -163,8 +167,8 @@ sr_status sr_match_host(sr_ctx *ctx, const uint8_t *h_left, const uint8_t *h_rig
  * values sr_match writes.
  *   Size limit: with A(b) = b rounded up to a multiple of 256 and e the
  *   bytes of one stored cost (4 for SR_VOL_F32, 2 for SR_VOL_F16/BF16),
- *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + 2*A(e*W*H*D) + 2*A(2*W*H) <= 32 MiB
- *   (e.g. 480x360 at D = 16, 320x180 at D = 64 with FP32 volumes); larger
+ *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + A(e*H*(W+D-1)*D) + 2*A(2*W*H) <= 32 MiB
+ *   (e.g. 640x480 at D = 16, 400x225 at D = 64 with FP32 volumes); larger
  *   frames are rejected with SR_ERR_UNSUPPORTED before any GPU work.
  *   The first call on a device looks up the array's device address with
  *   cudaGetSymbolAddress (with that device current); make that first call
@@ -195,7 +199,7 @@ typedef struct {
  * whole batch; sr_set_batch_schedule and sr_set_autotune select among
  * other schedules.  The context supplies D, the radii, gamma_d, gamma_r,
  * lr_thresh, vol_dtype and the stream; its width and height are not used.
- * Scratch for the whole batch (about sum of W*H*(2*D*e + 40) bytes, e as
+ * Scratch for the whole batch (about sum of ((2*W + D)*H*D*e + 40*W*H) bytes, e as
  * for sr_create) is allocated on first use and grown when a larger batch
  * arrives.  Results are identical to n sr_match calls.  Asynchronous.
  * Errors: SR_ERR_INVALID_ARG (n < 1, a bad pair), SR_ERR_OOM, SR_ERR_CUDA. */
@@ -299,7 +303,11 @@ sr_status sr_grad_plane(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_rig
  *   SR_BUF_MU_R       float [H][W]        block mean of i_r'
  *   SR_BUF_INV_R      float [H][W]        1/(n*sigma_r), 0 for a flat block
  *   SR_BUF_COST_L     float [H][W][D]     reference NCC volume (Eq. 3)
- *   SR_BUF_COST_R     float [H][W][D]     target NCC volume
+ *   SR_BUF_COST_R     float [H][W][D]     target NCC volume (after sr_match
+ *                                          rebuilt on the host from the
+ *                                          extended reference volume
+ *                                          sr_match computes: target cost
+ *                                          (u,v,d) = its column u + d)
  *   SR_BUF_AGG_L      float [H][W][D]     aggregated reference volume (Eq. 8),
  *   SR_BUF_AGG_R      float [H][W][D]     ... and target volume; these two are
  *                                          only written while the debug flag

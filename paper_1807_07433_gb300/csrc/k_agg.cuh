@@ -45,10 +45,12 @@ constexpr int kAggTX = 32, kAggTY = 4, kAggPX = 8, kAggPix = kAggTX * kAggTY;
 
 // SH: the tile reads a cost row sheared, pixel u at disparity d from column
 // u + d of an extended reference volume (the target view of Sec. II-B-1):
-// the ring slot holds D/16 boxes of 16 disparities x (32 + 2R + 16) pixels
-// of a 2-D tensor map, one box per 16-disparity chunk; odd chunks start one
-// pixel earlier, which moves their words to the other half of the shared-
-// memory banks (the chunk stride is a multiple of 32 words).
+// the ring slot holds D/CW boxes of CW disparities x BH pixels of a 2-D
+// tensor map, one box per CW-disparity chunk.  CW = 32 (128-byte box rows:
+// half the copies of CW = 16, and a lane's chunk words fall in distinct
+// banks) where MINB CTAs still fit an SM, else 16; with CW = 16, odd chunks
+// start one pixel earlier, which moves their words to the other half of the
+// banks (the chunk stride is a multiple of 32 words).
 template <int R, int D, typename VT, bool SH = false>
 struct AggCfg {
     static constexpr int SLOTS = D / 2;            // lanes per pixel group
@@ -59,11 +61,29 @@ struct AggCfg {
     static constexpr int WS = 2 * R + 1;           // window side
     static constexpr int TXE = kAggTX + 2 * R;     // ring row width (pixels)
     static constexpr int TYE = kAggTY + 2 * R;     // source rows per tile
-    static constexpr int NCH = D / 16;             // sheared: 16-disparity chunks
-    static constexpr int BH = TXE + 16;            // sheared: pixels of a chunk's box
-    // sheared: chunk stride, rounded up to 128 bytes (a tensor-map copy's
-    // destination alignment)
-    static constexpr int CSE = (int)(((BH * 16 * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
+    // sheared geometry for a chunk width cw: pixels of a box, chunk stride
+    // (rounded up to 128 bytes, a tensor-map copy's destination alignment)
+    static constexpr int shear_shift(int cw) { return (cw == 16 && D > 16) ? 1 : 0; }
+    static constexpr int shear_bh(int cw) { return TXE + cw - 1 + shear_shift(cw); }
+    static constexpr int shear_cse(int cw) {
+        return (int)(((shear_bh(cw) * cw * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
+    }
+    // shared memory of a CTA whose cost-ring slot holds ring elements
+    static constexpr size_t single_for(int ring) {
+        const size_t rings = ((size_t)ring * sizeof(VT) + 127) / 128 * 128;
+        const size_t ringsb = 2 * rings + (NW > 1 ? 2 : 1) * (size_t)(kAggTY * WS * kAggTX) * sizeof(float);
+        const size_t epib = (size_t)kAggPix * (D + 1) * sizeof(float);
+        const size_t uni = ((ringsb > epib ? ringsb : epib) + 15) / 16 * 16;
+        return uni + sizeof(float) * (((size_t)TYE * TXE + 3) / 4 * 4 + kAggPix) +
+               2 * sizeof(unsigned long long) + sizeof(int) * 4;
+    }
+    static constexpr int CW = (SH && D >= 32 &&
+                               MINB * (single_for((D / 32) * shear_cse(32)) + 1024) <= 228 * 1024)
+                                  ? 32 : 16;
+    static constexpr int NCH = D / CW;             // sheared: chunks
+    static constexpr int SHIFT = shear_shift(CW);  // sheared: odd chunks start a pixel earlier
+    static constexpr int BH = shear_bh(CW);        // sheared: pixels of a chunk's box
+    static constexpr int CSE = shear_cse(CW);      // sheared: chunk stride (elements)
     // elements of one cost row of the tile
     static constexpr int RING = SH ? NCH * CSE : TXE * D;
     // slot stride: RING rounded up to 128 bytes
@@ -87,6 +107,7 @@ struct AggCfg {
                                    sizeof(int) * (kStartSmem + 4);
     // kernels that do not walk a batch work list leave out its prefix array
     static constexpr size_t SMEM_SINGLE = SMEM - sizeof(int) * kStartSmem;
+    static_assert(single_for(RING) == SMEM_SINGLE, "shared-memory layouts disagree");
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
 };
 
@@ -238,11 +259,11 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
             // 16c + m sits in box row i + m + (c & 1).  As for BAND, columns
             // beyond the row's ends come from the neighbouring rows (or are
             // zeros) and meet zero weights.
-            mbar_arrive_expect_tx(bar, (unsigned)(C::NCH * C::BH * 16 * sizeof(VT)));
+            mbar_arrive_expect_tx(bar, (unsigned)(C::NCH * C::BH * C::CW * sizeof(VT)));
 #pragma unroll
             for (int c = 0; c < C::NCH; ++c)
-                tma_load_2d(ring + (j & 1) * C::RINGS + c * C::CSE, tmap, 16 * c,
-                            y * vpitch + x0 - R + 16 * c - (c & 1), bar);
+                tma_load_2d(ring + (j & 1) * C::RINGS + c * C::CSE, tmap, C::CW * c,
+                            y * vpitch + x0 - R + C::CW * c - C::SHIFT * (c & 1), bar);
             return;
         }
         VT *dst = ring + (j & 1) * C::RINGS + (xs - (x0 - R)) * D;
@@ -347,13 +368,16 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
             const float *ws = wring + (j % C::WSL) * C::WRING + bx;
             float2 cst[kAggPX + 2 * R];
             if (SH) {   // lane sl: disparities sl and sl + SLOTS (see the epilogue)
-                const VT *slot = ring + (j & 1) * C::RINGS + bx * 16;
+                constexpr int CW = C::CW;
+                const VT *slot = ring + (j & 1) * C::RINGS + bx * CW;
                 const int da = sl, db = sl + C::SLOTS;
-                const VT *ra = slot + (da >> 4) * C::CSE + ((da & 15) + ((da >> 4) & 1)) * 16 + (da & 15);
-                const VT *rb = slot + (db >> 4) * C::CSE + ((db & 15) + ((db >> 4) & 1)) * 16 + (db & 15);
+                const VT *ra = slot + (da / CW) * C::CSE +
+                               ((da % CW) + C::SHIFT * ((da / CW) & 1)) * CW + (da % CW);
+                const VT *rb = slot + (db / CW) * C::CSE +
+                               ((db % CW) + C::SHIFT * ((db / CW) & 1)) * CW + (db % CW);
 #pragma unroll
                 for (int i = 0; i < kAggPX + 2 * R; ++i)
-                    cst[i] = make_float2(load_one(ra + i * 16), load_one(rb + i * 16));
+                    cst[i] = make_float2(load_one(ra + i * CW), load_one(rb + i * CW));
             } else {
                 const VT *rs = ring + (j & 1) * C::RINGS + bx * D + 2 * sl;
 #pragma unroll
@@ -648,6 +672,20 @@ cudaError_t agg_launch_d(const VT *vol, const uint8_t *gl, int pitch, const floa
                                                                 lbl, dsub, agg, dbg, st, win,
                                                                 vpitch)))
     return cudaErrorInvalidValue;
+}
+
+// The box of the sheared kernel's tensor map: CW disparities x BH pixels.
+template <int R, int D, typename VT>
+void agg_shear_box_t(int *cw, int *bh) {
+    using C = AggCfg<R, D, VT, true>;
+    *cw = C::CW;
+    *bh = C::BH;
+}
+
+template <int D, typename VT>
+bool agg_shear_box_d(int agg_r, int *cw, int *bh) {
+    SR_AGG_R_SWITCH(agg_r, return (agg_shear_box_t<R_, D, VT>(cw, bh), true))
+    return false;
 }
 
 template <int D, typename VT>

@@ -7,4 +7,7 @@ cudaError_t launch_aggs_d32_bf16(const void *tmap, int vpitch, const float *gf, 
     return agg_shear_launch_d<32, __nv_bfloat16>(*static_cast<const CUtensorMap *>(tmap), vpitch, gf, W, H,
                                        agg_r, kd, kr, lbl, agg, dbg, st);
 }
+bool aggs_box_d32_bf16(int agg_r, int *cw, int *bh) {
+    return agg_shear_box_d<32, __nv_bfloat16>(agg_r, cw, bh);
+}
 }  // namespace sr

@@ -50,6 +50,15 @@ cudaError_t launch_aggs_d32_bf16(const void *tmap, int vpitch, const float *gf, 
 cudaError_t launch_aggs_d64_f32(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
 cudaError_t launch_aggs_d64_f16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
 cudaError_t launch_aggs_d64_bf16(const void *tmap, int vpitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *agg, const AggDebug &dbg, cudaStream_t st);
+bool aggs_box_d16_f32(int agg_r, int *cw, int *bh);
+bool aggs_box_d16_f16(int agg_r, int *cw, int *bh);
+bool aggs_box_d16_bf16(int agg_r, int *cw, int *bh);
+bool aggs_box_d32_f32(int agg_r, int *cw, int *bh);
+bool aggs_box_d32_f16(int agg_r, int *cw, int *bh);
+bool aggs_box_d32_bf16(int agg_r, int *cw, int *bh);
+bool aggs_box_d64_f32(int agg_r, int *cw, int *bh);
+bool aggs_box_d64_f16(int agg_r, int *cw, int *bh);
+bool aggs_box_d64_bf16(int agg_r, int *cw, int *bh);
 cudaError_t launch_agg_band_f32(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 cudaError_t launch_agg_band_f16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
 cudaError_t launch_agg_band_bf16(const void *tmap, const uint8_t *gl, int pitch, const float *gf, int W, int H, int agg_r, float kd, float kr, int16_t *lbl, float *dsub, const AggDebug &dbg, const AggWin &win, cudaStream_t st);
@@ -291,17 +300,31 @@ bool encode_volume_map(CUtensorMap *m, void *vol, int vt, int W, int H, int D, i
 }  // namespace
 
 // Tensor map of the extended reference volume [H][W+D-1][D] viewed as
-// [H*(W+D-1)][D], box 16 disparities x (32 + 2 agg_r + 16) pixels, zeros
-// outside (see launch_agg_shear).
+// [H*(W+D-1)][D], box CW disparities x BH pixels of the sheared kernel's
+// configuration, zeros outside (see launch_agg_shear).
 bool sr::encode_shear_map(void *tmap, const void *volx, int vt, int W, int H, int D, int agg_r) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
+    int cw = 0, bh = 0;
+    bool ok = false;
+#define SR_BOX(DD)                                                                    \
+    ok = vt == kVolF32 ? sr::aggs_box_d##DD##_f32(agg_r, &cw, &bh)                    \
+       : vt == kVolF16 ? sr::aggs_box_d##DD##_f16(agg_r, &cw, &bh)                    \
+                       : sr::aggs_box_d##DD##_bf16(agg_r, &cw, &bh)
+    switch (D) {
+        case 16: SR_BOX(16); break;
+        case 32: SR_BOX(32); break;
+        case 64: SR_BOX(64); break;
+        default: break;
+    }
+#undef SR_BOX
+    if (!ok) return false;
     const CUtensorMapDataType dt = vt == sr::kVolF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : vt == sr::kVolF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)(W + D - 1) * H};
     const cuuint64_t strides[1] = {(cuuint64_t)D * sr::vol_elem_bytes(vt)};
-    const cuuint32_t box[2] = {16, (cuuint32_t)(32 + 2 * agg_r + 16)};
+    const cuuint32_t box[2] = {(cuuint32_t)cw, (cuuint32_t)bh};
     const cuuint32_t estr[2] = {1, 1};
     return fn(static_cast<CUtensorMap *>(tmap), dt, 2, const_cast<void *>(volx), dims, strides,
               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

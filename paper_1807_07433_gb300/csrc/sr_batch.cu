@@ -20,9 +20,10 @@
 //     capture streams, largest first, so that one pair's kernels fill the
 //     tails of another's; still descriptor-driven, so the graph replays with
 //     new images and planes as long as the sequence of sizes repeats;
-//   C (variants 6-7): per pair, the six kernels of sr_match itself with the
-//     pair's pointers and plane as kernel parameters, on 1 or 4 forked capture
-//     streams, largest first.  The graph holds the parameters, so a call with
+//   C (variants 6-7): per pair, the five kernels of sr_match itself (one
+//     extended NCC volume read by both aggregations) with the pair's pointers
+//     and plane as kernel parameters, on 1 or 4 forked capture streams,
+//     largest first.  The graph holds the parameters, so a call with
 //     other pointers or planes re-captures it and updates the executable graph
 //     in place (cudaGraphExecUpdate; a fresh instantiation if that fails).
 // The tuner times each candidate on the caller's own batch the first time a
@@ -520,7 +521,7 @@ sr_status sr_batch_info(sr_ctx *c, char *buf, size_t size) {
              b->graph_n, b->variant, sched, per_pair(b->variant) ? 1 : ((b->variant & 1) ? 2 : 1),
              per_pair(b->variant) ? 1 : (b->variant >> 1) & 1,
              per_pair(b->variant) ? pair_streams(b->variant) : 1,
-             sched_c(b->variant) ? 6 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
+             sched_c(b->variant) ? 5 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
              sr::ncc_batch_occupancy(D, c->p.ncc_radius, c->p.vol_dtype),
              sr::agg_batch_occupancy(D, c->p.agg_radius, c->p.vol_dtype), b->sms, ms,
              b->pool_bytes);

@@ -135,9 +135,10 @@ cudaError_t launch_agg_shear(const void *tmap, int vt, const float *guide_f32, i
                              int D, int agg_r, float gamma_d, float gamma_r, int16_t *lbl,
                              float *agg, const AggDebug &dbg, cudaStream_t st);
 // The tensor map launch_agg_shear reads: the extended volume volx
-// [H][W+D-1][D] viewed as [H*(W+D-1)][D], box 16 disparities x
-// (32 + 2 agg_r + 16) pixels, zeros outside.  tmap: 64-byte aligned storage
-// of a CUtensorMap (128 bytes).  False when the driver refuses the map.
+// [H][W+D-1][D] viewed as [H*(W+D-1)][D], box of the sheared kernel's chunk
+// (16 or 32 disparities x the pixels a row needs), zeros outside.  tmap:
+// 64-byte aligned storage of a CUtensorMap (128 bytes).  False when the
+// driver refuses the map or the parameters have no sheared kernel.
 bool encode_shear_map(void *tmap, const void *volx, int vt, int W, int H, int D, int agg_r);
 
 // The band kernel of the restricted search: tiles with band >= 0 aggregate
