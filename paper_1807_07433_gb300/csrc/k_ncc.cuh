@@ -27,7 +27,8 @@
 // each block column ox.  Each column of the sliding block is read from shared
 // memory once (2r+1 loads) and feeds up to (2r+1)^2 FMAs, so the kernel is
 // FMA-bound rather than shared-memory-bound.  Disparities are processed in
-// chunks of DC so that the accumulators stay in registers.
+// chunks of DC (16 or 32, see NccOcc) so that the accumulators stay in
+// registers.
 //
 // Tiles: 32 x 4 output pixels per CTA (128 threads); the fixed image tile and
 // the sliding image tile (widened by D-1 columns) are staged in shared memory
@@ -41,6 +42,20 @@
 namespace sr {
 
 constexpr int kNccTX = 32, kNccTY = 4, kNccThreads = kNccTX * kNccTY;
+
+// Register budget by block radius.  At 5 x 5 and 7 x 7 blocks a
+// 16-disparity chunk of accumulators leaves room for seven CTAs per SM (at
+// most 72 registers; 7 x 7 measured 13 % faster than 32-disparity chunks at
+// five CTAs).  3 x 3 blocks fit many CTAs anyway, and 9 x 9 and 11 x 11
+// blocks (81 and 121 centred values in registers) keep 32-disparity chunks
+// and the compiler's own budget: a bound would spill them, and narrower
+// chunks made the compiler unroll into twice the registers.
+template <int RN>
+struct NccOcc {
+    static constexpr bool NARROW = RN == 2 || RN == 3;
+    static constexpr int DC = NARROW ? 16 : 32;    // disparity chunk (at most D)
+    static constexpr int MINB = NARROW ? 7 : 0;    // CTAs per SM of k_ncc (0: no bound)
+};
 
 template <int RN, int D>
 struct NccSmem {
@@ -67,7 +82,8 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
                                          int dlo = 0, int dhi = D - 1) {
     using S = NccSmem<RN, D>;
     constexpr int B = S::B, FW = S::FW, SW = S::SW, TH = S::TH, XW = S::XW;
-    constexpr int DC = D < 32 ? D : 32;          // disparity chunk held in registers
+    // disparity chunk held in registers (see NccOcc)
+    constexpr int DC = D < NccOcc<RN>::DC ? D : NccOcc<RN>::DC;
     const int tid = threadIdx.x;
     const int WE = W + D - 1;
 
@@ -180,7 +196,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
 }
 
 template <int RN, int D, bool TARGET, typename VT>
-__global__ void __launch_bounds__(kNccThreads)
+__global__ void __launch_bounds__(kNccThreads, NccOcc<RN>::MINB)
 k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
       const float *__restrict__ mu_l, const float *__restrict__ inv_l,
       const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
