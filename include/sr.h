@@ -154,6 +154,22 @@ sr_status sr_match_restricted(sr_ctx *ctx, const uint8_t *d_left, const uint8_t 
 sr_status sr_match_host(sr_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
                         float *h_disp);
 
+/* Streaming form of sr_match_host for a sequence of frames (video): queues
+ * the upload of h_left/h_right, the match and the download of the disparity
+ * map into h_disp, and returns without waiting for them.  Uploads and
+ * downloads run on two copy streams the context creates on first use, so
+ * that the next frame's upload and the previous frame's download overlap
+ * this frame's kernels (which run on the context's stream, in call order).
+ * At most two frames are in flight: when the call returns, every frame
+ * queued two or more calls earlier has finished (its disparity map is in its
+ * h_disp and its host images may be reused); sr_synchronize finishes all of
+ * them.  Host buffers should be pinned (cudaHostAlloc / cudaHostRegister)
+ * for the copies to overlap.  Results are those of sr_match_host.  Errors as
+ * sr_match_host; a device-side timeout of an earlier frame is reported by
+ * the call that waits for it. */
+sr_status sr_match_host_async(sr_ctx *ctx, const uint8_t *h_left, const uint8_t *h_right,
+                              float *h_disp);
+
 /* sr_match for callers that cannot allocate device memory.  (The paper has
  * no counterpart: this entry point concerns only memory ownership.)
  * Some callers cannot call cudaMalloc -- a host that fixes the library's

@@ -255,6 +255,13 @@ void free_all(sr_ctx *c) {
         if (q) cudaFree(q);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_up[i]) cudaEventDestroy(c->ev_up[i]);
+        if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
+        if (c->ev_down[i]) cudaEventDestroy(c->ev_down[i]);
+    }
+    if (c->up) cudaStreamDestroy(c->up);
+    if (c->down) cudaStreamDestroy(c->down);
     sr_batch_free(c);
 }
 
@@ -486,6 +493,8 @@ sr_status sr_stage_times(sr_ctx *c, float *ms, int n, int *count) {
 sr_status sr_synchronize(sr_ctx *c) {
     if (!c) return SR_ERR_INVALID_ARG;
     SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
+    if (c->up) SR_TRY(c, cudaStreamSynchronize(c->up), "cudaStreamSynchronize(upload)");
+    if (c->down) SR_TRY(c, cudaStreamSynchronize(c->down), "cudaStreamSynchronize(download)");
     return take_device_error(c);
 }
 
@@ -626,14 +635,24 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
     return SR_OK;
 }
 
+// Two slots of host-buffer staging (allocated on first use).
+static sr_status ensure_staging(sr_ctx *c) {
+    if (c->stage_l) return SR_OK;
+    const size_t npx = (size_t)c->p.width * c->p.height;
+    SR_TRY(c, dalloc(&c->stage_l, 2 * npx), "cudaMalloc(stage)");
+    SR_TRY(c, dalloc(&c->stage_r, 2 * npx), "cudaMalloc(stage)");
+    SR_TRY(c, dalloc(&c->stage_disp, 2 * npx), "cudaMalloc(stage)");
+    return SR_OK;
+}
+
 sr_status sr_match_host(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right, float *h_disp) {
     if (!c || !h_left || !h_right || !h_disp) return SR_ERR_INVALID_ARG;
     const size_t npx = (size_t)c->p.width * c->p.height;
-    if (!c->stage_l) {
-        SR_TRY(c, dalloc(&c->stage_l, npx), "cudaMalloc(stage)");
-        SR_TRY(c, dalloc(&c->stage_r, npx), "cudaMalloc(stage)");
-        SR_TRY(c, dalloc(&c->stage_disp, npx), "cudaMalloc(stage)");
-    }
+    sr_status s0 = ensure_staging(c);
+    if (s0 != SR_OK) return s0;
+    // frames still queued by sr_match_host_async use the staging too
+    if (c->up) SR_TRY(c, cudaStreamSynchronize(c->up), "cudaStreamSynchronize(upload)");
+    if (c->down) SR_TRY(c, cudaStreamSynchronize(c->down), "cudaStreamSynchronize(download)");
     SR_TRY(c, cudaMemcpyAsync(c->stage_l, h_left, npx, cudaMemcpyHostToDevice, c->st), "H2D left");
     SR_TRY(c, cudaMemcpyAsync(c->stage_r, h_right, npx, cudaMemcpyHostToDevice, c->st), "H2D right");
     sr_status s = sr_match(c, c->stage_l, c->stage_r, c->p.width, c->stage_disp, nullptr);
@@ -643,6 +662,50 @@ sr_status sr_match_host(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right
            "D2H disp");
     SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
     return take_device_error(c);
+}
+
+sr_status sr_match_host_async(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right,
+                              float *h_disp) {
+    if (!c || !h_left || !h_right || !h_disp) return SR_ERR_INVALID_ARG;
+    const size_t npx = (size_t)c->p.width * c->p.height;
+    sr_status s0 = ensure_staging(c);
+    if (s0 != SR_OK) return s0;
+    if (!c->up) {
+        SR_TRY(c, cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking), "cudaStreamCreate");
+        SR_TRY(c, cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int i = 0; i < 2; ++i) {
+            SR_TRY(c, cudaEventCreateWithFlags(&c->ev_up[i], cudaEventDisableTiming), "cudaEventCreate");
+            SR_TRY(c, cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming), "cudaEventCreate");
+            SR_TRY(c, cudaEventCreateWithFlags(&c->ev_down[i], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    const int k = c->slot;
+    uint8_t *dl = c->stage_l + k * npx, *dr = c->stage_r + k * npx;
+    float *dd = c->stage_disp + k * npx;
+    if (c->frames_queued >= 2) {
+        // the frame queued two calls ago used this slot: let it finish, so
+        // that its result is in its host buffer and its inputs are free
+        SR_TRY(c, cudaEventSynchronize(c->ev_down[k]), "cudaEventSynchronize");
+        sr_status s = take_device_error(c);
+        if (s != SR_OK) return s;
+        // upload after that frame's kernels have read the slot's images
+        SR_TRY(c, cudaStreamWaitEvent(c->up, c->ev_comp[k], 0), "cudaStreamWaitEvent");
+    }
+    SR_TRY(c, cudaMemcpyAsync(dl, h_left, npx, cudaMemcpyHostToDevice, c->up), "H2D left");
+    SR_TRY(c, cudaMemcpyAsync(dr, h_right, npx, cudaMemcpyHostToDevice, c->up), "H2D right");
+    SR_TRY(c, cudaEventRecord(c->ev_up[k], c->up), "cudaEventRecord");
+    SR_TRY(c, cudaStreamWaitEvent(c->st, c->ev_up[k], 0), "cudaStreamWaitEvent");
+    sr_status s = sr_match(c, dl, dr, c->p.width, dd, nullptr);
+    if (s != SR_OK) return s;
+    SR_TRY(c, cudaEventRecord(c->ev_comp[k], c->st), "cudaEventRecord");
+    SR_TRY(c, cudaStreamWaitEvent(c->down, c->ev_comp[k], 0), "cudaStreamWaitEvent");
+    SR_TRY(c, cudaMemcpyAsync(h_disp, dd, npx * sizeof(float), cudaMemcpyDeviceToHost, c->down),
+           "D2H disp");
+    SR_TRY(c, cudaEventRecord(c->ev_down[k], c->down), "cudaEventRecord");
+    // the next match on this slot writes dd: after this download
+    c->slot = k ^ 1;
+    ++c->frames_queued;
+    return SR_OK;
 }
 
 sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {

@@ -32,8 +32,16 @@ struct sr_ctx {
     float *dsub = nullptr;
     int16_t *lbl_l = nullptr, *lbl_r = nullptr;
     float *agg_l = nullptr, *agg_r = nullptr;
+    // host-buffer staging: slot 0 for sr_match_host; slots 0 and 1 for
+    // sr_match_host_async (frame k uses slot k mod 2)
     uint8_t *stage_l = nullptr, *stage_r = nullptr;
     float *stage_disp = nullptr;
+    // sr_match_host_async: upload and download streams, per-slot events
+    // (upload done, match done, download done), next slot, frames queued
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_up[2] = {}, ev_comp[2] = {}, ev_down[2] = {};
+    int slot = 0;
+    long long frames_queued = 0;
     int debug = 0;
     int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
     bool matched = false, agg_valid = false;

@@ -28,7 +28,7 @@ SR_DEBUG_NO_BAND = 4
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
            "sr_match_restricted",
-           "sr_match_host", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
+           "sr_match_host", "sr_match_host_async", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
            "sr_fit_alpha", "sr_fit_roll",
            "sr_get_buffer", "sr_set_debug",
@@ -83,6 +83,7 @@ def load(path: str | None = None):
                 "sr_set_camera": (i, [vp, d, d, d, d]),
                 "sr_match": (i, [vp, vp, vp, i, vp, vp]),
                 "sr_match_host": (i, [vp, vp, vp, vp]),
+                "sr_match_host_async": (i, [vp, vp, vp, vp]),
                 "sr_match_restricted": (i, [vp, vp, vp, i, vp, i, vp, vp]),
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
@@ -187,6 +188,12 @@ def sr_match_restricted(ctx, d_left, d_right, pitch_bytes: int, d_centre, radius
 def sr_match_host(ctx, h_left, h_right, h_disp) -> None:
     _check(ctx, load().sr_match_host(ctx, _ptr(h_left), _ptr(h_right), _ptr(h_disp)),
            "sr_match_host")
+
+
+def sr_match_host_async(ctx, h_left, h_right, h_disp) -> None:
+    """Queue one frame of host buffers (see sr.h); sr_synchronize finishes it."""
+    _check(ctx, load().sr_match_host_async(ctx, _ptr(h_left), _ptr(h_right), _ptr(h_disp)),
+           "sr_match_host_async")
 
 
 def sr_match_noalloc(params: sr_params, alpha0: float, alpha1: float, delta: float, d_left,

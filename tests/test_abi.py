@@ -86,6 +86,7 @@ def test_null_arguments(lib):
     assert lib.sr_set_camera(None, 700.0, 120.0, 0.0, 0.0) == sr.SR_ERR_INVALID_ARG
     assert lib.sr_match(None, None, None, 64, None, None) == sr.SR_ERR_INVALID_ARG
     assert lib.sr_match_host(None, None, None, None) == sr.SR_ERR_INVALID_ARG
+    assert lib.sr_match_host_async(None, None, None, None) == sr.SR_ERR_INVALID_ARG
     assert lib.sr_reconstruct(None, None, None) == sr.SR_ERR_INVALID_ARG
     n = ctypes.c_size_t(0)
     assert lib.sr_get_buffer(None, 0, None, ctypes.byref(n)) == sr.SR_ERR_INVALID_ARG

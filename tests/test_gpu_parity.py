@@ -169,6 +169,40 @@ def test_match_host_equals_device_path():
         np.testing.assert_array_equal(hd.numpy()[fin], g["dfull"][fin])
 
 
+def test_match_host_async_stream_of_frames():
+    """The streaming host call: five frames of three different pairs queued
+    back to back equal sr_match_host frame by frame; when a call returns, the
+    frame two calls back is complete."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    scenes = [synth.small(203, 77, D=64, ncc_r=3, agg_r=5, seed=s) for s in (61, 62, 63)]
+    pairs = [synth.make_pair(w.scene)[:2] for w in scenes]
+    w = scenes[0]
+    H, W = pairs[0][0].shape
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        want = []
+        hd = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        for left, right in pairs:
+            sr.sr_match_host(m.ctx, torch.from_numpy(left).pin_memory(),
+                             torch.from_numpy(right).pin_memory(), hd)
+            want.append(hd.numpy().copy())
+        ins = [(torch.from_numpy(l).pin_memory(), torch.from_numpy(r).pin_memory())
+               for l, r in pairs]
+        outs = [torch.full((H, W), -7.0, dtype=torch.float32).pin_memory() for _ in range(5)]
+        for k in range(5):
+            sr.sr_match_host_async(m.ctx, ins[k % 3][0], ins[k % 3][1], outs[k])
+            if k >= 2:   # frame k - 2 is complete
+                np.testing.assert_array_equal(outs[k - 2].numpy(), want[(k - 2) % 3])
+        sr.sr_synchronize(m.ctx)
+        for k in range(5):
+            np.testing.assert_array_equal(outs[k].numpy(), want[k % 3])
+        # the synchronous call after queued frames
+        sr.sr_match_host(m.ctx, ins[1][0], ins[1][1], hd)
+        np.testing.assert_array_equal(hd.numpy(), want[1])
+
+
 def test_repeatable():
     """Same inputs give bit-identical outputs (no atomics or races in the path)."""
     w = CASES[0]
