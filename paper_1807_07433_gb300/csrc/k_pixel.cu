@@ -226,9 +226,12 @@ dim3 grid_for(int w, int h) { return dim3((w + kBX - 1) / kBX, (h + kBY - 1) / k
 // 4-5) of both images, for one 32 x 8 tile of extended block centres: the
 // tile's left rows and its warped-target rows (each with the block halo,
 // clamp-to-edge) are staged in shared memory once, the row shifts once per
-// row; every statistic is then computed from shared memory with the same
-// operations in the same order as stats_left_px / stats_right_px, and the
-// warped image is written for the columns this tile owns.
+// row, and the warped image is written for the columns this tile owns.
+// Left statistics: sliding-window sums, separable -- column sums of the
+// block's rows for every staged column, then each centre sums 2 RN + 1 of
+// them -- in exact integers, so they equal stats_left_px's.  Warped-target
+// statistics: the centred two-pass form of stats_right_px, in its order (a
+// running sum of squares would cancel in FP32 on smooth blocks).
 template <int RN>
 __global__ void __launch_bounds__(kBX * kBY)
 k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch, int W,
@@ -239,6 +242,8 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     constexpr int n = B * B;
     __shared__ int s_l[TH][TW];           // left intensities
     __shared__ float s_r[TH][TW];         // warped target intensities
+    __shared__ unsigned s_cs[kBY][TW];    // left column sums over the block rows
+    __shared__ unsigned s_cs2[kBY][TW];   // ... of squares
     __shared__ int s_k[TH];               // row shift: integer part
     __shared__ float s_w[TH];             // row shift: fraction
     const int WE = W + D - 1;
@@ -280,6 +285,19 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
         }
     }
     __syncthreads();
+    for (int i = tid; i < kBY * TW; i += kBX * kBY) {   // column sums of B rows
+        const int r = i / TW, c = i % TW;
+        unsigned cs = 0, cs2 = 0;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const unsigned val = (unsigned)s_l[r + j][c];
+            cs += val;
+            cs2 += val * val;
+        }
+        s_cs[r][c] = cs;
+        s_cs2[r][c] = cs2;
+    }
+    __syncthreads();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int xi = x0 + tx, v = y0 + ty;
     if (xi >= WE || v >= H) return;
@@ -287,13 +305,10 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     {
         unsigned su = 0, s2 = 0;
 #pragma unroll
-        for (int j = 0; j < B; ++j)
-#pragma unroll
-            for (int i = 0; i < B; ++i) {
-                const unsigned val = (unsigned)s_l[ty + j][tx + i];
-                su += val;
-                s2 += val * val;
-            }
+        for (int i = 0; i < B; ++i) {
+            su += s_cs[ty][tx + i];
+            s2 += s_cs2[ty][tx + i];
+        }
         const long long q = (long long)n * s2 - (long long)su * su;   // n^2 var, exact
         const float var = (float)q / (float)(n * n);
         inv_l[(size_t)v * WE + xi] = (var < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)q);
