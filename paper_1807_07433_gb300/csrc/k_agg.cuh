@@ -37,6 +37,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "sr_internal.cuh"
 
 namespace sr {
@@ -275,8 +277,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
     // Weights (Eqs. 9-10) that source row j contributes with: for output row
     // py the tap row is dyi = j - py.  w = exp(-r^2/gd^2 - dg^2/gr^2)
     // = exp2(-(r^2 kd + dg^2 kr)), zero for neighbours outside the image.
-    // Warp k computes rows py = k, k + NW, ...; lane = pixel column.
-    auto make_weights = [&](int j) {
+    // Warp k computes rows py = k, k + NW, ...; lane = pixel column.  In a
+    // tile whose pixels and neighbourhoods all lie inside the image
+    // (interior == true) no weight needs the border test.
+    auto make_weights = [&](int j, auto interior) {
         float *wslot = wring + (j % C::WSL) * C::WRING;
 #pragma unroll
         for (int k = 0; k < 4 / C::NW; ++k) {
@@ -284,8 +288,8 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
             const int dyi = j - py;
             if (dyi < 0 || dyi >= C::WS) continue;
             const int px = lane, u = x0 + px, v = y0 + py, y = v + dyi - R;
-            const bool rowok = (u < W) && (v < H) && (y >= 0) && (y < H);
-            const bool inner = rowok && (u - R >= 0) && (u + R < W);
+            const bool rowok = decltype(interior)::value || ((u < W) && (v < H) && (y >= 0) && (y < H));
+            const bool inner = decltype(interior)::value || (rowok && (u - R >= 0) && (u + R < W));
             const float gc = guide[(py + R) * C::TXE + px + R];
             const float *grow = guide + (py + dyi) * C::TXE + px;
             const float fy = (float)((dyi - R) * (dyi - R)) * kd;
@@ -333,8 +337,15 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
             if (c < xs || c >= xe) ring[i] = VT(0.0f);
         }
     }
+    const bool interior = x0 - R >= 0 && x0 + kAggTX + R <= W && y0 - R >= 0 && y0 + kAggTY + R <= H;
+    auto weights_of_row = [&](int j) {
+        if (interior)
+            make_weights(j, std::integral_constant<bool, true>());
+        else
+            make_weights(j, std::integral_constant<bool, false>());
+    };
     __syncthreads();
-    if (C::WSL == 2) make_weights(0);
+    if (C::WSL == 2) weights_of_row(0);
     __syncthreads();
 
     // ---- main loop: stream the tile's source rows --------------------------
@@ -356,10 +367,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 issue_row(j + 1);
             }
-            if (C::WSL == 2) make_weights(j + 1);
+            if (C::WSL == 2) weights_of_row(j + 1);
         }
         if (C::WSL == 1) {   // the single slot was last read before the previous barrier
-            make_weights(j);
+            weights_of_row(j);
             __syncthreads();
         }
         const int y = y0 - R + j;
