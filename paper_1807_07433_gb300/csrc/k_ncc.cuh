@@ -66,8 +66,7 @@ struct NccSmem {
     static constexpr int XW = kNccTX + D - 1;           // sliding-block centres per tile row
     float fix_s[TH][FW];
     float sld_s[TH][SW];
-    float smu_s[kNccTY][XW];                            // sliding-block mean
-    float sinv_s[kNccTY][XW];                           // sliding-block 1/(n sigma)
+    float2 sst_s[kNccTY][XW];                           // sliding block: (mean - K, 1/(n sigma))
 };
 
 // One 32 x 4 tile at (x0, y0).  All threads of the CTA take part (barrier).
@@ -121,8 +120,8 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
             const int r = i / XW, t = i % XW;
             const int y = clampi(y0 + r, 0, H - 1);
             const int xi = clampi(x0 + t, 0, WE - 1);
-            sm.smu_s[r][t] = mu_s[(size_t)y * WE + xi];
-            sm.sinv_s[r][t] = inv_s[(size_t)y * WE + xi];
+            sm.sst_s[r][t] = make_float2(mu_s[(size_t)y * WE + xi] - kNccOffset,
+                                         inv_s[(size_t)y * WE + xi]);
         }
     }
     __syncthreads();
@@ -132,8 +131,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     // Statistics rows (block centres extended by D-1 columns, see launch_stats):
     // the fixed block sits at u, the sliding block at u+d (target) / u-d (reference).
     // sliding centre of disparity d at smem index base + so, so = d or -d
-    const float *mu_s_row = &sm.smu_s[ty][TARGET ? tx : tx + D - 1];
-    const float *inv_s_row = &sm.sinv_s[ty][TARGET ? tx : tx + D - 1];
+    const float2 *st_s_row = &sm.sst_s[ty][TARGET ? tx : tx + D - 1];
 
     // Centred fixed block and the sum of its (rounded) centred values.
     float a[B][B];
@@ -181,14 +179,14 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
         float cst[DC];
 #pragma unroll
         for (int i = 0; i < DC; ++i) {
-            const int d = d0 + i;
-            const int so = TARGET ? d : -d;
-            const float num = fmaf(-sa, mu_s_row[so] - kNccOffset, acc[i]);
-            cst[i] = num * inv_f * inv_s_row[so];
+            const int so = TARGET ? d0 + i : -(d0 + i);
+            const float2 ss = st_s_row[so];
+            const float num = fmaf(-sa, ss.x, acc[i]);
+            cst[i] = num * inv_f * ss.y;
             // extended volume: a sliding centre u - d >= W has no statistics
             // of its own; no cost is taken from there, but readers meet the
             // entry with weight zero, so it is stored as 0 (finite)
-            if (!TARGET && u - d >= W) cst[i] = 0.0f;
+            if (!TARGET && u - (d0 + i) >= W) cst[i] = 0.0f;
         }
 #pragma unroll
         for (int i = 0; i < DC; i += 8) store8(out + d0 + i, cst + i);
