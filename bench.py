@@ -351,17 +351,23 @@ def run_reference(args, w):
 
 
 def precision_report(steps: int, warmup: int):
-    """Precision form on the 1920x1080x64 workload: FP32 / FP16 / BF16 volumes,
-    each timed (CUDA events, L2 flushed between steps) and compared with the
-    full-frame FP64 oracle: integer-disparity mismatch rate, subpixel RMS and
-    3-D point error (mm, f = 700 px, baseline 120 mm)."""
+    """Precision form on the 1280x720x64 and 1920x1080x64 workloads: FP32 /
+    FP16 / BF16 volumes, each timed (CUDA events, L2 flushed between steps)
+    and compared with the full-frame FP64 oracle: integer-disparity mismatch
+    rate, subpixel RMS and 3-D point error (mm, f = 700 px, baseline 120 mm)."""
+    from paper_1807_07433_gb300 import synth
+    return {"report": "precision", "reference": "FP64 oracle, full frame", "steps": steps,
+            "warmup": warmup,
+            "workloads": [_precision_workload(w, steps, warmup) for w in (synth.C2, synth.C3)]}
+
+
+def _precision_workload(w, steps: int, warmup: int):
     import numpy as np
     import torch
 
     import oracle
     from paper_1807_07433_gb300 import sr, synth
 
-    w = synth.C3
     W, H, D = w.scene.W, w.scene.H, w.D
     left, right, _ = synth.make_pair(w.scene)
     oracle.build()
@@ -416,9 +422,10 @@ def precision_report(steps: int, warmup: int):
             "xyz_p99_mm": float(np.quantile(dx, 0.99)),
             "compared_pixels": int(both.sum()),
         }
-    return {"report": "precision", "workload": w.name, "W": W, "H": H, "D": D,
-            "reference": "FP64 oracle, full frame", "oracle_s": round(t_orc, 2),
-            "steps": steps, "warmup": warmup, "forms": forms}
+    return {"workload": w.name, "W": W, "H": H, "D": D, "oracle_s": round(t_orc, 2),
+            "forms": forms}
+
+
 
 
 def _gen_pair(scene):
