@@ -130,14 +130,23 @@ __device__ __forceinline__ void lrc_px(const int16_t *__restrict__ lbl_l,
     if (wta_out) wta_out[i] = (int16_t)l;
 }
 
+// Each thread checks kLrcPX pixels of one row, kBX apart (so that every
+// access of a warp stays coalesced): independent loads in flight per thread
+// and a grid of about one wave, for a kernel that is all memory latency.
+constexpr int kLrcPX = 4;
+
 __global__ void k_lrc_post(const int16_t *__restrict__ lbl_l, const int16_t *__restrict__ lbl_r,
                            const float *__restrict__ dsub, int W, int H, double alpha0,
                            double alpha1, double delta, float lr_thresh, float *__restrict__ disp,
                            int16_t *__restrict__ wta_out) {
-    const int u = blockIdx.x * kBX + threadIdx.x;
+    const int u0 = blockIdx.x * kBX * kLrcPX + threadIdx.x;
     const int v = blockIdx.y * kBY + threadIdx.y;
-    if (u >= W || v >= H) return;
-    lrc_px(lbl_l, lbl_r, dsub, W, alpha0, alpha1, delta, lr_thresh, disp, wta_out, u, v);
+    if (v >= H) return;
+#pragma unroll
+    for (int i = 0; i < kLrcPX; ++i) {
+        const int u = u0 + i * kBX;
+        if (u < W) lrc_px(lbl_l, lbl_r, dsub, W, alpha0, alpha1, delta, lr_thresh, disp, wta_out, u, v);
+    }
 }
 
 // ---- batched forms: persistent 32x8 blocks over a batch's flat tile list --
@@ -392,8 +401,8 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
 cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,
                             int H, double alpha0, double alpha1, double delta, float lr_thresh,
                             float *disp, int16_t *wta_out, cudaStream_t st) {
-    k_lrc_post<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(lbl_l, lbl_r, dsub, W, H, alpha0, alpha1,
-                                                         delta, lr_thresh, disp, wta_out);
+    k_lrc_post<<<grid_for(ceil_div(W, kLrcPX), H), dim3(kBX, kBY), 0, st>>>(
+        lbl_l, lbl_r, dsub, W, H, alpha0, alpha1, delta, lr_thresh, disp, wta_out);
     return cudaGetLastError();
 }
 
