@@ -117,7 +117,8 @@ sr_status sr_set_camera(sr_ctx *ctx, double f_px, double baseline, double u0, do
  *                    disparity l_ref of the reference view.
  * The NCC cost (Eq. 3) is computed once, as the reference volume over
  * W + D - 1 columns; the target view of Sec. II-B-1 reads it at column
- * u + d.  Five kernels: prep, ncc, agg_ref, agg_tgt, lrc_post.  The first
+ * u + d.  Four kernels: prep, ncc, agg_tgt, agg_ref; the last one also
+ * runs the L-R check and the post-processing on its WTA labels.  The first
  * call builds the tensor map of that read.  Asynchronous on the context's
  * stream.  Errors: SR_ERR_INVALID_ARG for null images/output or pitch < W,
  * SR_ERR_CUDA for a failed launch or a driver that refuses the tensor map. */

@@ -484,6 +484,16 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
                 if (den < 0.0f) ds += (cm - cp) / den;
             }
             dsub[o] = ds;
+            if (!WIN && win.post.disp) {   // Eq. 11 and Sec. II-C (see AggPost)
+                const int l = best + dlo, ur = u - l;
+                bool ok = false;
+                if (ur >= 0)
+                    ok = fabsf((float)(l - (int)win.post.lbl_r[(size_t)v * W + ur])) <=
+                         win.post.lr_thresh;
+                const double sv = win.post.alpha0 + win.post.alpha1 * (double)v - win.post.delta;
+                win.post.disp[o] = ok ? (float)((double)ds + sv) : __int_as_float(0x7fc00000);
+                if (win.post.wta) win.post.wta[o] = (int16_t)l;
+            }
         }
     }
     if (agg) {

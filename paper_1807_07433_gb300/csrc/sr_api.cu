@@ -233,7 +233,7 @@ int agg_batch_occupancy(int D, int agg_r, int vt) {
 
 namespace {
 
-const char *const kStageNames = "prep,ncc,agg_ref,agg_tgt,lrc_post";
+const char *const kStageNames = "prep,ncc,agg_tgt,agg_ref";
 
 }  // namespace
 
@@ -382,7 +382,7 @@ const char *sr_stage_names(void) { return kStageNames; }
 
 int sr_kernels_per_match(const sr_ctx *c) {
     (void)c;
-    return 5;   // prep (warp + statistics), ncc (extended volume), 2x agg, lrc_post
+    return 4;   // prep (warp + statistics), ncc (extended volume), agg_tgt, agg_ref (+ L-R check)
 }
 
 sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
@@ -533,19 +533,25 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
            "ncc");
     SR_TRY(c, mark(), "cudaEventRecord");
     const sr::AggDebug dbg = agg_debug(c);
-    SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
-                             p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
-                             dbg, st, sr::AggWin(), WE),
-           "agg_ref");
-    SR_TRY(c, mark(), "cudaEventRecord");
+    // target view first: the reference-view kernel runs the L-R check and
+    // the post-processing in its epilogue, on the finished target labels
     SR_TRY(c, sr::launch_agg_shear(&c->tmap_x, p.vol_dtype, c->rw, W, H, D, p.agg_radius,
                                    p.gamma_d, p.gamma_r, c->lbl_r, keep ? c->agg_r : nullptr, dbg,
                                    st),
            "agg_tgt");
     SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->alpha0, c->alpha1,
-                                  c->delta, p.lr_thresh, d_disp, d_wta_or_null, st),
-           "lrc_post");
+    sr::AggWin post;
+    post.post.lbl_r = c->lbl_r;
+    post.post.disp = d_disp;
+    post.post.wta = d_wta_or_null;
+    post.post.alpha0 = c->alpha0;
+    post.post.alpha1 = c->alpha1;
+    post.post.delta = c->delta;
+    post.post.lr_thresh = p.lr_thresh;
+    SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
+                             p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
+                             dbg, st, post, WE),
+           "agg_ref");
     SR_TRY(c, mark(), "cudaEventRecord");
     c->matched = true;
     c->vol_ext = true;

@@ -20,7 +20,7 @@
 //     capture streams, largest first, so that one pair's kernels fill the
 //     tails of another's; still descriptor-driven, so the graph replays with
 //     new images and planes as long as the sequence of sizes repeats;
-//   C (variants 6-7): per pair, the five kernels of sr_match itself (one
+//   C (variants 6-7): per pair, the four kernels of sr_match itself (one
 //     extended NCC volume read by both aggregations) with the pair's pointers
 //     and plane as kernel parameters, on 1 or 4 forked capture streams,
 //     largest first.  The graph holds the parameters, so a call with
@@ -227,13 +227,21 @@ cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     const int WE = P.W + D - 1;
     if ((e = sr::launch_ncc(false, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
                             P.H, D, p.ncc_radius, P.vol_l, p.vol_dtype, st, nullptr, WE)) != cudaSuccess) return e;
-    if ((e = sr::launch_agg(P.vol_l, p.vol_dtype, P.left, P.pitch, nullptr, P.W, P.H, D,
-                            p.agg_radius, p.gamma_d, p.gamma_r, P.lbl_l, P.dsub, nullptr, dbg,
-                            st, sr::AggWin(), WE)) != cudaSuccess) return e;
+    // target view first; the reference view runs the L-R check and the
+    // post-processing in its epilogue, as in sr_match
     if ((e = sr::launch_agg_shear(&b->tmaps[k], p.vol_dtype, P.rw, P.W, P.H, D, p.agg_radius,
                                   p.gamma_d, p.gamma_r, P.lbl_r, nullptr, dbg, st)) != cudaSuccess) return e;
-    return sr::launch_lrc_post(P.lbl_l, P.lbl_r, P.dsub, P.W, P.H, P.alpha0, P.alpha1, P.delta,
-                               p.lr_thresh, P.disp, P.wta, st);
+    sr::AggWin post;
+    post.post.lbl_r = P.lbl_r;
+    post.post.disp = P.disp;
+    post.post.wta = P.wta;
+    post.post.alpha0 = P.alpha0;
+    post.post.alpha1 = P.alpha1;
+    post.post.delta = P.delta;
+    post.post.lr_thresh = p.lr_thresh;
+    return sr::launch_agg(P.vol_l, p.vol_dtype, P.left, P.pitch, nullptr, P.W, P.H, D,
+                          p.agg_radius, p.gamma_d, p.gamma_r, P.lbl_l, P.dsub, nullptr, dbg, st,
+                          post, WE);
 }
 
 cudaError_t launch_stages(sr_ctx *c, SrBatch *b, int n, int variant, cudaStream_t st) {
@@ -521,7 +529,7 @@ sr_status sr_batch_info(sr_ctx *c, char *buf, size_t size) {
              b->graph_n, b->variant, sched, per_pair(b->variant) ? 1 : ((b->variant & 1) ? 2 : 1),
              per_pair(b->variant) ? 1 : (b->variant >> 1) & 1,
              per_pair(b->variant) ? pair_streams(b->variant) : 1,
-             sched_c(b->variant) ? 5 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
+             sched_c(b->variant) ? 4 * b->graph_n : sched_b(b->variant) ? 7 * b->graph_n : 7,
              sr::ncc_batch_occupancy(D, c->p.ncc_radius, c->p.vol_dtype),
              sr::agg_batch_occupancy(D, c->p.agg_radius, c->p.vol_dtype), b->sms, ms,
              b->pool_bytes);

@@ -7,7 +7,7 @@
 #include "../../include/sr.h"
 #include "sr_internal.cuh"
 
-constexpr int kStages = 5;    // stages of one sr_match with profiling events
+constexpr int kStages = 4;    // stages of one sr_match with profiling events
 
 struct SrBatch;               // batched-form state, defined in sr_batch.cu
 void sr_batch_free(sr_ctx *c);

@@ -105,12 +105,24 @@ struct AggDebug {
 // radius < 0: the full search 0..D-1.  band (nullable): per 32 x 4 tile, the
 // first disparity of the band kernel's 16-wide slice (-1: the tile needs the
 // full-D kernel); the full-D kernel skips tiles with band >= 0.
+// Eq. 11 L-R check and Sec. II-C post-processing fused into the epilogue of
+// the reference-view aggregation (disp != nullptr): the target labels lbl_r
+// must be complete before that kernel starts.  The arithmetic is that of
+// launch_lrc_post.
+struct AggPost {
+    const int16_t *lbl_r = nullptr;
+    float *disp = nullptr;           // full disparity, NaN where rejected
+    int16_t *wta = nullptr;          // optional copy of the reference labels
+    double alpha0 = 0.0, alpha1 = 0.0, delta = 0.0;
+    float lr_thresh = 0.0f;
+};
 struct AggWin {
     const int16_t *centre = nullptr;
     int centre_const = 0;
     int radius = -1;
     int dfull = 0;
     const int *band = nullptr;
+    AggPost post;                    // fused L-R check (full search only)
 };
 constexpr int kBandD = 16;        // disparities per band-kernel slice
 constexpr int kAggTileX = 32, kAggTileY = 4;   // aggregation tile (pixels)

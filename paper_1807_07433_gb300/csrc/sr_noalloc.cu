@@ -113,12 +113,21 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
                         delta, rw, mu_l, inv_l, mu_r, inv_r, st) != cudaSuccess ||
         sr::launch_ncc(false, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
                        p.ncc_radius, volx, p.vol_dtype, st, nullptr, WEi) != cudaSuccess ||
-        sr::launch_agg(volx, p.vol_dtype, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius, p.gamma_d,
-                       p.gamma_r, lbl_l, dsub, nullptr, dbg, st, sr::AggWin(), WEi) != cudaSuccess ||
         sr::launch_agg_shear(&tmap, p.vol_dtype, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d,
-                             p.gamma_r, lbl_r, nullptr, dbg, st) != cudaSuccess ||
-        sr::launch_lrc_post(lbl_l, lbl_r, dsub, Wi, Hi, alpha0, alpha1, delta, p.lr_thresh,
-                            d_disp, d_wta_or_null, st) != cudaSuccess)
+                             p.gamma_r, lbl_r, nullptr, dbg, st) != cudaSuccess)
+        return SR_ERR_CUDA;
+    // the reference view last, with the L-R check and post-processing in its
+    // epilogue (as in sr_match)
+    sr::AggWin post;
+    post.post.lbl_r = lbl_r;
+    post.post.disp = d_disp;
+    post.post.wta = d_wta_or_null;
+    post.post.alpha0 = alpha0;
+    post.post.alpha1 = alpha1;
+    post.post.delta = delta;
+    post.post.lr_thresh = p.lr_thresh;
+    if (sr::launch_agg(volx, p.vol_dtype, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius,
+                       p.gamma_d, p.gamma_r, lbl_l, dsub, nullptr, dbg, st, post, WEi) != cudaSuccess)
         return SR_ERR_CUDA;
     return SR_OK;
 }
