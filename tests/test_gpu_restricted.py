@@ -105,3 +105,25 @@ def test_restricted_bad_arguments():
             with pytest.raises(sr.SrError) as e:
                 m.match_restricted(img, img, r)
             assert e.value.status == sr.SR_ERR_INVALID_ARG
+
+
+def test_window_gives_a_smaller_search_range():
+    """A search of 0..D'-1 with D' = 24 on a D = 32 context: every centre at
+    floor((D'-1)/2) = 11 with radius floor(D'/2) = 12 makes each window
+    exactly [0, 23], so the result is the oracle's full search with D = 24."""
+    w32 = synth.small(150, 61, D=32, ncc_r=2, agg_r=4, seed=37)
+    w24 = synth.small(150, 61, D=24, ncc_r=2, agg_r=4, seed=37)
+    left, right, _ = synth.make_pair(w32.scene)
+    g = _run(w32, left, right, np.full(left.shape, 11), 12)
+    o = oracle.match(oracle_params(w24), left, right,
+                     want=("lbl_l", "lbl_r", "gap_l", "gap_r", "den_l", "dsub", "dfull"))
+    agree, bad = label_report(g["wta"], o.lbl_l, o.gap_l)
+    assert agree >= AGREE_MIN and bad == 0, (agree, bad)
+    agree_r, bad_r = label_report(g["lbl_r"], o.lbl_r, o.gap_r)
+    assert agree_r >= AGREE_MIN and bad_r == 0, (agree_r, bad_r)
+    ok = (g["wta"] == o.lbl_l) & (o.gap_l >= TAU_TIE) & \
+        ((np.abs(o.den_l) >= DEN_MIN) | (o.den_l == 0))
+    assert np.abs(g["dsub"][ok] - o.dsub[ok]).max() <= TOL_DSUB
+    both = ok & np.isfinite(g["dfull"]) & np.isfinite(o.dfull)
+    assert both.mean() > 0.5
+    assert np.abs(g["dfull"][both] - o.dfull[both]).max() <= TOL_DSUB

@@ -65,3 +65,18 @@ def test_wta_window_equals_numpy_argmax(seed):
             assert d == lo + int(np.argmax(c[lo:hi + 1]))
             rest = np.delete(c[lo:hi + 1], d - lo)
             assert gap == (c[d] - rest.max() if len(rest) else np.inf)
+
+
+def test_window_zero_to_dprime_equals_a_search_of_dprime():
+    """Centre floor((D'-1)/2) and radius floor(D'/2) give every pixel the
+    window [0, D'-1]: the result equals the full search with D = D' (the
+    aggregated costs of a disparity do not depend on D)."""
+    w16 = synth.small(64, 40, D=16, ncc_r=2, agg_r=3, seed=43)
+    w11 = synth.small(64, 40, D=11, ncc_r=2, agg_r=3, seed=43, delta=4.0)
+    left, right, _ = synth.make_pair(w16.scene)
+    want = ("lbl_l", "lbl_r", "dsub", "valid", "dfull")
+    full = oracle.match(oracle_params(w11), left, right, want=want)
+    res = oracle.match(oracle_params(w16), left, right, want=want,
+                       centre=np.full(left.shape, (11 - 1) // 2), radius=11 // 2)
+    for k in want:
+        np.testing.assert_array_equal(getattr(res, k), getattr(full, k), err_msg=k)
