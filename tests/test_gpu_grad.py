@@ -4,9 +4,12 @@ central differences of the GPU's own objective.
 Tolerances (FP32 terms, FP64 sums):
   L        |L_gpu - L_orc| <= TOL_AGG * (pixels in the set): each pixel's
            c_agg carries at most the aggregated-cost error of the forward path
-  dL/dalpha  rel 2e-3: per-term FP32 error ~1e-6 relative; the sum cancels
+  dL/dalpha  rel 1e-3, against the oracle's analytic gradient and against
+           central differences (of the oracle's FP64 objective, and of the
+           GPU's own): per-term FP32 error ~1e-6 relative; the sum cancels
            (terms of both signs), so alpha is taken off the optimum where the
-           gradient is large
+           gradient is large (measured: <= 3e-6 against the oracle, 1.3e-5
+           against the GPU's FP32 differences)
   images   |g_gpu - g_orc| <= 2e-3 |g_orc| + 1e-3 max|g_orc|
 """
 import numpy as np
@@ -46,7 +49,7 @@ def _check(w, left, right, dstar, a0, a1):
     Lo, dao, glo, gro = _orc_grad(w, left, right, dstar, a0, a1)
     n_set = int(((dstar >= 0) & (dstar < w.D)).sum())
     assert abs(L - Lo) <= TOL_AGG * max(n_set, 1), (L, Lo)
-    np.testing.assert_allclose(da, dao, rtol=2e-3, atol=1e-9)
+    np.testing.assert_allclose(da, dao, rtol=1e-3, atol=1e-9)
     for g, go in ((gl, glo), (gr, gro)):
         tol = 2e-3 * np.abs(go) + 1e-3 * max(np.abs(go).max(), 1e-12)
         bad = np.abs(g - go) > tol
@@ -106,8 +109,8 @@ def test_alpha_gradient_matches_gpu_central_differences():
     f = lambda x0, x1: _gpu_grad(w, left, right, dstar, x0, x1, image_grads=False)[0]
     fd0 = (f(a0 + h0, a1) - f(a0 - h0, a1)) / (2 * h0)
     fd1 = (f(a0, a1 + h1) - f(a0, a1 - h1)) / (2 * h1)
-    assert da[0] == pytest.approx(fd0, rel=2e-3)
-    assert da[1] == pytest.approx(fd1, rel=2e-3)
+    assert da[0] == pytest.approx(fd0, rel=1e-3)
+    assert da[1] == pytest.approx(fd1, rel=1e-3)
 
 
 def test_grad_is_deterministic_in_L_and_alpha():
@@ -213,3 +216,44 @@ def test_full_size_crop_matches_oracle():
     a0 = w.scene.alpha0 + rng.uniform(-1.5, 1.5)
     a1 = w.scene.alpha1 + rng.uniform(-0.01, 0.01)
     _check(w, left, right, dstar, a0, a1)
+
+
+def test_full_size_crop_gradient_matches_oracle_central_differences():
+    """dL/dalpha of the GPU adjoint on the 1280x720 crop (rows 560-679, cols
+    560-719) against central differences with step 1e-3 of the FP64 oracle's
+    objective.  alpha0 starts at the perturbed plane (seed 5) and moves to
+    where no row shift of the rows the crop reads lies within 1.5 steps of an
+    integer, so that no difference crosses a kink of the linear warp."""
+    import oracle
+    w = synth.C2
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    dstar = np.full((H, W), -1, np.int16)
+    dstar[560:680, 560:720] = int(w.delta)
+    rng = np.random.default_rng(5)
+    a0 = w.scene.alpha0 + rng.uniform(-1.5, 1.5)
+    a1 = w.scene.alpha1 + rng.uniform(-0.01, 0.01)
+    reach = w.agg_r + w.ncc_r
+    v = np.arange(560 - reach, 680 + reach, dtype=np.float64)
+    h0 = 1e-3
+    h1 = h0 / v.max()
+    for _ in range(2000):
+        s = a0 + a1 * v - w.delta
+        frac = s - np.floor(s)
+        if np.minimum(frac, 1.0 - frac).min() > 1.5 * h0:
+            break
+        a0 += 0.0071
+    else:
+        raise AssertionError("no alpha0 clear of the warp kinks")
+    _, da = _gpu_grad(w, left, right, dstar, a0, a1, image_grads=False)
+    ds32 = dstar.astype(np.int32)
+
+    def objective(x0, x1):
+        p = oracle_params(w)
+        p.alpha0, p.alpha1 = x0, x1
+        return oracle.objective(p, left.astype(np.float64), right.astype(np.float64), ds32)
+
+    fd0 = (objective(a0 + h0, a1) - objective(a0 - h0, a1)) / (2 * h0)
+    fd1 = (objective(a0, a1 + h1) - objective(a0, a1 - h1)) / (2 * h1)
+    assert da[0] == pytest.approx(fd0, rel=1e-3)
+    assert da[1] == pytest.approx(fd1, rel=1e-3)
