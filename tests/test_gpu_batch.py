@@ -142,3 +142,35 @@ def test_batch_rejects_bad_pairs():
         with pytest.raises(sr.SrError) as e:
             sr.sr_match_batch(m.ctx, [bad])
         assert e.value.status == sr.SR_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("vt", [0, 1])
+def test_batch_at_the_mixed_workload_sizes(vt):
+    """One pair at each frame size of the 64-pair workload (672x376, 1280x720,
+    1920x1080, 2208x1242), D = 64, NCC 7x7, bilateral 11x11, planes drawn as
+    in that workload: the batch (tuned schedule) equals sr_match per pair bit
+    for bit, FP32 and FP16 volumes."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    rng = np.random.default_rng(1000)
+    pairs = []
+    for k, (W, H) in enumerate([(672, 376), (1280, 720), (1920, 1080), (2208, 1242)]):
+        sc = synth.Scene(W, H, float(rng.uniform(10, 40)), float(rng.uniform(0.02, 0.1)), 20,
+                         True, 1000 + k)
+        left, right, _ = synth.make_pair(sc)
+        pairs.append((left, right, sc.alpha0, sc.alpha1, 8.0))
+    want = []
+    for left, right, a0, a1, dl in pairs:
+        H, W = left.shape
+        with sr.Matcher(W, H, 64, 3, 5, 4.0, 12.0, vol_dtype=vt,
+                        stream=torch.cuda.current_stream()) as m:
+            m.set_plane(a0, a1, dl)
+            wta = torch.empty((H, W), dtype=torch.int16, device="cuda")
+            disp = m.match(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(), wta=wta)
+            torch.cuda.synchronize()
+            want.append((disp.cpu().numpy(), wta.cpu().numpy()))
+    with sr.Matcher(8, 8, 64, 3, 5, 4.0, 12.0, vol_dtype=vt,
+                    stream=torch.cuda.current_stream()) as m:
+        sr.sr_set_autotune(m.ctx, True)
+        _same(_batch(m.ctx, pairs), want)
+        _same(_batch(m.ctx, pairs, order=[3, 1, 0, 2]), want)

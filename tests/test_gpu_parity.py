@@ -121,17 +121,19 @@ def test_two_volume_identity_on_gpu():
     assert np.abs(g["cost_l"]).max() <= 1.0 + 1e-5
 
 
-def test_full_size_sampled_pixels():
-    """The 1280x720x64 workload in the benchmark's launch configuration,
-    checked at sampled pixels that the oracle evaluates one by one."""
+@pytest.mark.parametrize("w", [synth.C2, synth.C3], ids=lambda w: w.name)
+def test_full_size_sampled_pixels(w):
+    """The 1280x720x64 workload in the benchmark's launch configuration, and
+    the 1920x1080x64 precision workload, checked at sampled pixels that the
+    oracle evaluates one by one."""
     import oracle
-    w = synth.C2
     left, right, _ = synth.make_pair(w.scene)
     g = run_gpu(w, left, right)
     H, W = left.shape
     rng = np.random.default_rng(2024)
-    us = np.concatenate([rng.integers(0, W, 150), [0, W - 1, 0, W - 1, 5, W - 6, 640, 641]])
-    vs = np.concatenate([rng.integers(0, H, 150), [0, 0, H - 1, H - 1, 3, H - 4, 360, 360]])
+    us = np.concatenate([rng.integers(0, W, 150),
+                         [0, W - 1, 0, W - 1, 5, W - 6, W // 2, W // 2 + 1]])
+    vs = np.concatenate([rng.integers(0, H, 150), [0, 0, H - 1, H - 1, 3, H - 4, H // 2, H // 2]])
     o = oracle.match_pixels(oracle_params(w), left, right, us, vs)
     gl = g["wta"][vs, us]
     diff = gl != o["lbl_l"]
