@@ -187,17 +187,32 @@ sr_status sr_match_host_async(sr_ctx *ctx, const uint8_t *h_left, const uint8_t 
  *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + A(e*H*(W+D-1)*D) + 2*A(2*W*H) <= 32 MiB
  *   (e.g. 640x480 at D = 16, 400x225 at D = 64 with FP32 volumes); larger
  *   frames are rejected with SR_ERR_UNSUPPORTED before any GPU work.
- *   The first call on a device looks up the array's device address with
- *   cudaGetSymbolAddress (with that device current); make that first call
- *   before any stream capture.
+ *   The first call in a CUDA context (the device's primary context, or a
+ *   driver-API context made current by the caller) looks up the array's
+ *   device address with cudaGetSymbolAddress, with that context current,
+ *   and keeps it under the context's unique ID; a context created later
+ *   (e.g. after cudaDeviceReset) gets its own look-up.  Make the first call
+ *   in each context before any stream capture.
  *   Every call reuses the same array and leaves its contents behind; nothing
  *   in it needs to start at zero.  Calls whose GPU work overlaps (other
  *   streams, or other threads without ordering) race on the array.
+ *   Bounded device-side waits that run out set a sticky timeout word (also
+ *   a fixed device variable, not an allocation); the call itself returns
+ *   before the GPU work ends, so a timeout is reported by
+ *   sr_noalloc_status, not by this call.
  * Asynchronous on cuda_stream (NULL = legacy default stream).  Errors:
  * SR_ERR_INVALID_ARG, SR_ERR_UNSUPPORTED (parameters or size), SR_ERR_CUDA. */
 sr_status sr_match_noalloc(const sr_params *params, double alpha0, double alpha1, double delta,
                            const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                            float *d_disp, int16_t *d_wta_or_null, void *cuda_stream);
+
+/* Status of the sr_match_noalloc calls made in the current CUDA context:
+ * synchronises cuda_stream, then returns SR_ERR_TIMEOUT if a bounded wait of
+ * any such call ran out since the last sr_noalloc_status (the results of
+ * that call are undefined), clearing the condition, else SR_OK.  Allocates
+ * nothing (two 4-byte copies between a host variable and the device word).
+ * Errors: SR_ERR_CUDA. */
+sr_status sr_noalloc_status(void *cuda_stream);
 
 /* One stereo pair of a batch (all pointers device pointers owned by the
  * caller; layouts as for sr_match). */
@@ -251,33 +266,6 @@ sr_status sr_batch_info(sr_ctx *ctx, char *buf, size_t size);
  * NaN or not positive.  Asynchronous.  SR_ERR_STATE if no camera is set. */
 sr_status sr_reconstruct(sr_ctx *ctx, const float *d_disp, float *d_xyz);
 
-/* Gradient of the aggregated matching cost with respect to the road plane,
- * for refining alpha (Sec. II-A, Eq. 2) by gradient ascent.  The paper fits
- * alpha once from a disparity map (Sec. II-A) and has no gradient; this is
- * the adjoint of its own cost, by the chain rule through the warp (Sec.
- * II-A), the NCC (Eqs. 3-5) and the bilateral aggregation of the reference
- * volume (Eqs. 8-10, guide = left image):
- *   L(alpha) = sum over pixels p with d_dstar[p] >= 0 of c_agg(p, d_dstar[p]),
- * with the disparities d_dstar held fixed (the plane hypothesis is every
- * pixel at residual delta; the winning labels of sr_match are another set).
- * The warp and block statistics are recomputed at the context's current
- * plane (sr_set_plane), so the call does not depend on an earlier sr_match.
- *   d_left, d_right   8-bit images, pitch_bytes >= W, as for sr_match
- *   d_dstar           int16 [H][W] dense residual disparities; a value
- *                     outside 0..D-1 (e.g. -1) leaves the pixel out of L
- *   h_out3            host double[3]: L, dL/dalpha0, dL/dalpha1
- *   d_grad_left, d_grad_right
- *                     float [H][W] dense or NULL: dL/di_l and dL/di_r, the
- *                     images read as real values (FP32 atomics: the last
- *                     bits vary from run to run; L and dL/dalpha are summed
- *                     in FP64 in a fixed order and do not)
- * Arithmetic is FP32 per term with FP64 sums.  The objective is piecewise
- * smooth in alpha: it has kinks where a row shift alpha0 + alpha1 v - delta
- * crosses an integer.  Synchronises the context's stream (h_out3 is host
- * memory).  The context's scratch is reused (the buffers of the last
- * sr_match are no longer available to sr_get_buffer afterwards); the first
- * call allocates about 12*W*H bytes more, plus 4*W*H*D bytes for an FP32
- * cost volume when the context stores 16-bit volumes. */
 /* Road-plane fitting from a disparity map, Sec. II-A: the paper fits alpha
  * of Eq. 2 by least squares with RANSAC on reliable correspondences, and the
  * roll angle by fitting a plane to a near-field patch of the disparity map.
@@ -308,6 +296,33 @@ sr_status sr_fit_alpha(sr_ctx *ctx, const float *d_disp, int n_hyp, const int32_
 sr_status sr_fit_roll(sr_ctx *ctx, const float *d_disp, int u_lo, int v_lo, int u_hi, int v_hi,
                       double *h_gamma, double *h_roll, int *h_n);
 
+/* Gradient of the aggregated matching cost with respect to the road plane,
+ * for refining alpha (Sec. II-A, Eq. 2) by gradient ascent.  The paper fits
+ * alpha once from a disparity map (Sec. II-A) and has no gradient; this is
+ * the adjoint of its own cost, by the chain rule through the warp (Sec.
+ * II-A), the NCC (Eqs. 3-5) and the bilateral aggregation of the reference
+ * volume (Eqs. 8-10, guide = left image):
+ *   L(alpha) = sum over pixels p with d_dstar[p] >= 0 of c_agg(p, d_dstar[p]),
+ * with the disparities d_dstar held fixed (the plane hypothesis is every
+ * pixel at residual delta; the winning labels of sr_match are another set).
+ * The warp and block statistics are recomputed at the context's current
+ * plane (sr_set_plane), so the call does not depend on an earlier sr_match.
+ *   d_left, d_right   8-bit images, pitch_bytes >= W, as for sr_match
+ *   d_dstar           int16 [H][W] dense residual disparities; a value
+ *                     outside 0..D-1 (e.g. -1) leaves the pixel out of L
+ *   h_out3            host double[3]: L, dL/dalpha0, dL/dalpha1
+ *   d_grad_left, d_grad_right
+ *                     float [H][W] dense or NULL: dL/di_l and dL/di_r, the
+ *                     images read as real values (FP32 atomics: the last
+ *                     bits vary from run to run; L and dL/dalpha are summed
+ *                     in FP64 in a fixed order and do not)
+ * Arithmetic is FP32 per term with FP64 sums.  The objective is piecewise
+ * smooth in alpha: it has kinks where a row shift alpha0 + alpha1 v - delta
+ * crosses an integer.  Synchronises the context's stream (h_out3 is host
+ * memory).  The context's scratch is reused (the buffers of the last
+ * sr_match are no longer available to sr_get_buffer afterwards); the first
+ * call allocates about 12*W*H bytes more, plus 4*W*H*D bytes for an FP32
+ * cost volume when the context stores 16-bit volumes. */
 sr_status sr_grad_plane(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right,
                         int pitch_bytes, const int16_t *d_dstar, double *h_out3,
                         float *d_grad_left, float *d_grad_right);

@@ -729,11 +729,11 @@ static int line_through(const float *disp, int W, int i1, int i2, double *a0, do
     return 1;
 }
 
-/* Inlier test of pixel (v, d) against a model, decided in single precision:
- * |d - fma(a1, v, a0)| <= tau with a0, a1 rounded to float (the precision of
- * the disparity map itself). */
-static int is_inlier(float d, int v, float a0f, float a1f, float tau) {
-    return !isnan(d) && fabsf(d - fmaf(a1f, (float)v, a0f)) <= tau;
+/* Inlier test of pixel (v, d) against the model d = a0 + a1 v, in double
+ * precision: |d - (a0 + a1 v)| <= tau (the definition; the disparity map
+ * itself is float). */
+static int is_inlier(float d, int v, double a0, double a1, double tau) {
+    return !isnan(d) && fabs((double)d - (a0 + a1 * (double)v)) <= tau;
 }
 
 /* RANSAC over n_hyp given point pairs (pairs[2h], pairs[2h+1]): counts[h] =
@@ -753,9 +753,8 @@ int orc_fit_alpha(const float *disp, int W, int H, int n_hyp, const int32_t *pai
             counts[h] = -1;
             continue;
         }
-        const float a0f = (float)a0, a1f = (float)a1;
         int32_t c = 0;
-        for (size_t i = 0; i < npx; ++i) c += is_inlier(disp[i], (int)(i / W), a0f, a1f, tau);
+        for (size_t i = 0; i < npx; ++i) c += is_inlier(disp[i], (int)(i / W), a0, a1, tau);
         counts[h] = c;
         if (c > best_n) { best_n = c; best = h; }
     }
@@ -763,11 +762,10 @@ int orc_fit_alpha(const float *disp, int W, int H, int n_hyp, const int32_t *pai
     if (best < 0) return -1;
     double a0, a1;
     line_through(disp, W, pairs[2 * best], pairs[2 * best + 1], &a0, &a1);
-    const float a0f = (float)a0, a1f = (float)a1;
     double s0 = 0, s1 = 0, s2 = 0, t0 = 0, t1 = 0;   /* n, sum v, sum v^2, sum d, sum v d */
     for (size_t i = 0; i < npx; ++i) {
         const int v = (int)(i / W);
-        if (!is_inlier(disp[i], v, a0f, a1f, tau)) continue;
+        if (!is_inlier(disp[i], v, a0, a1, tau)) continue;
         const double d = disp[i];
         s0 += 1.0; s1 += v; s2 += (double)v * v; t0 += d; t1 += (double)v * d;
     }

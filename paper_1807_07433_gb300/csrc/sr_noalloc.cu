@@ -6,22 +6,28 @@
 // loops that must not stall on the allocator), plug-in hosts whose own
 // allocator owns the device, or code that must not create a context object
 // at all.  For them this file keeps every intermediate of one match (warped
-// target, block statistics, both cost volumes, both label maps, subpixel
-// map) in one file-scope device array of fixed size, kSrNoallocScratchBytes.
-// The array exists on every GPU that loads this library, until the process
-// exits.  The kernels are the ones sr_match launches; only where their
-// scratch lives differs.
+// target, block statistics, the cost volume, both label maps, subpixel map)
+// in one file-scope device array of fixed size, kSrNoallocScratchBytes, and
+// the timeout flag of the bounded waits in a file-scope device word.  Both
+// exist on every GPU that loads this library, until the process exits.  The
+// kernels are the ones sr_match launches; only where their scratch lives
+// differs.
 //
-// The host only sees a stand-in for the array's name, never its device
-// address, so the address is looked up with cudaGetSymbolAddress the first
-// time the entry point runs on a device (with that device current) and
-// cached per device.  Because that first call does the look-up, make it
-// before any stream capture.
+// The host only sees stand-ins for those names, never their device
+// addresses, so the addresses are looked up with cudaGetSymbolAddress the
+// first time the entry point runs in a CUDA context (with that context
+// current) and cached under the context's unique ID (cuCtxGetId): a
+// context created later -- after a device reset, or a driver-API context
+// other than the device's primary one -- gets its own look-up, since the
+// module, and with it the arrays, is loaded anew there.  Because that first
+// call in a context does the look-up, make it before any stream capture.
 //
 // Every call shares the one array and leaves its contents behind.  No part of
 // it needs to start at zero: each stage writes every element that a later
 // stage reads.  Calls whose work overlaps on the GPU (different streams, or
-// different host threads without ordering) race on the array.
+// different host threads without ordering) race on the array.  The timeout
+// word is sticky: a bounded wait that runs out sets it, and only
+// sr_noalloc_status reads and clears it.
 #include <cuda.h>
 #include <math.h>
 
@@ -33,31 +39,74 @@
 namespace {
 
 constexpr size_t kSrNoallocScratchBytes = (size_t)32 << 20;   // 32 MiB
-constexpr int kMaxDevices = 64;
+constexpr int kCacheSlots = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kSrNoallocScratchBytes];
+static __device__ int g_noalloc_err;
+
+// Device addresses of the two arrays in one CUDA context.
+struct Addrs {
+    unsigned long long ctx_id;
+    void *scratch;
+    int *err;
+};
 
 std::mutex g_lookup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
+Addrs g_cache[kCacheSlots] = {};
+int g_cache_used = 0, g_cache_next = 0;
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
 
-// Device address of the scratch array on the current device (looked up once).
-cudaError_t scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+template <typename Fn>
+Fn driver_fn(const char *name) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return reinterpret_cast<Fn>(p);
+}
+
+// Unique ID of the context current on this thread; false if none is current
+// or the driver cannot tell.
+bool current_context_id(unsigned long long *id) {
+    static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device addresses of the scratch array and the timeout word in the current
+// context (looked up once per context; without a context ID, on every call).
+cudaError_t noalloc_addrs(Addrs *out) {
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lock(g_lookup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+    if (have_id)
+        for (int i = 0; i < g_cache_used; ++i)
+            if (g_cache[i].ctx_id == id) {
+                *out = g_cache[i];
+                return cudaSuccess;
+            }
+    Addrs a{};
+    cudaError_t e = cudaGetSymbolAddress(&a.scratch, g_noalloc_scratch);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&a.err, g_noalloc_err);
+    if (e != cudaSuccess) return e;
+    // the look-up makes the device's primary context current if none was
+    if (!have_id) have_id = current_context_id(&id);
+    if (have_id) {
+        a.ctx_id = id;
+        const int slot = g_cache_used < kCacheSlots ? g_cache_used++ : g_cache_next++ % kCacheSlots;
+        g_cache[slot] = a;
     }
-    *out = g_scratch_addr[dev];
+    *out = a;
     return cudaSuccess;
 }
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 bool pos_finite(float x) { return isfinite(x) && x > 0.0f; }
 
@@ -88,9 +137,9 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     const size_t need = 2 * b_img + 4 * b_ext + b_vol + 2 * b_lbl;
     if (need > kSrNoallocScratchBytes) return SR_ERR_UNSUPPORTED;   // frame too large
 
-    void *base = nullptr;
-    if (scratch_address(&base) != cudaSuccess) return SR_ERR_CUDA;
-    unsigned char *q = static_cast<unsigned char *>(base);
+    Addrs addrs;
+    if (noalloc_addrs(&addrs) != cudaSuccess) return SR_ERR_CUDA;
+    unsigned char *q = static_cast<unsigned char *>(addrs.scratch);
     auto take = [&q](size_t b) { unsigned char *r = q; q += b; return r; };
     float *rw = reinterpret_cast<float *>(take(b_img));
     float *dsub = reinterpret_cast<float *>(take(b_img));
@@ -103,7 +152,8 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     int16_t *lbl_r = reinterpret_cast<int16_t *>(take(b_lbl));
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const sr::AggDebug dbg;   // default bounded waits; no error word to report through
+    sr::AggDebug dbg;   // default bounded waits, reporting to the sticky timeout word
+    dbg.err = addrs.err;
     const int Wi = p.width, Hi = p.height, Di = p.max_disp, WEi = Wi + Di - 1;
     // the sheared view of the extended volume (a host-side descriptor)
     CUtensorMap tmap;
@@ -130,4 +180,18 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
                        p.gamma_d, p.gamma_r, lbl_l, dsub, nullptr, dbg, st, post, WEi) != cudaSuccess)
         return SR_ERR_CUDA;
     return SR_OK;
+}
+
+extern "C" sr_status sr_noalloc_status(void *cuda_stream) {
+    if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) return SR_ERR_CUDA;
+    Addrs addrs;
+    if (noalloc_addrs(&addrs) != cudaSuccess) return SR_ERR_CUDA;
+    int flag = 0;
+    if (cudaMemcpy(&flag, addrs.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SR_ERR_CUDA;
+    if (!flag) return SR_OK;
+    const int zero = 0;
+    if (cudaMemcpy(addrs.err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SR_ERR_CUDA;
+    return SR_ERR_TIMEOUT;
 }

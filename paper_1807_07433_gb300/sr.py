@@ -28,7 +28,8 @@ SR_DEBUG_NO_BAND = 4
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
            "sr_match_restricted",
-           "sr_match_host", "sr_match_host_async", "sr_match_noalloc", "sr_match_batch", "sr_set_autotune",
+           "sr_match_host", "sr_match_host_async", "sr_match_noalloc", "sr_noalloc_status",
+           "sr_match_batch", "sr_set_autotune",
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
            "sr_fit_alpha", "sr_fit_roll",
            "sr_get_buffer", "sr_set_debug",
@@ -87,6 +88,7 @@ def load(path: str | None = None):
                 "sr_match_restricted": (i, [vp, vp, vp, i, vp, i, vp, vp]),
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
+                "sr_noalloc_status": (i, [vp]),
                 "sr_match_batch": (i, [vp, i, ctypes.POINTER(sr_pair_desc)]),
                 "sr_set_autotune": (i, [vp, i, ctypes.c_char_p]),
                 "sr_batch_info": (i, [vp, ctypes.c_char_p, sz]),
@@ -205,6 +207,13 @@ def sr_match_noalloc(params: sr_params, alpha0: float, alpha1: float, delta: flo
                                          _ptr(d_left), _ptr(d_right), int(pitch_bytes),
                                          _ptr(d_disp), _ptr(d_wta_or_null),
                                          _stream_handle(cuda_stream)), "sr_match_noalloc")
+
+
+def sr_noalloc_status(cuda_stream=None) -> None:
+    """Synchronise the stream; raise SrError(SR_ERR_TIMEOUT) if a bounded wait
+    of an sr_match_noalloc call in the current context ran out since the last
+    check (the condition is then cleared)."""
+    _check(None, load().sr_noalloc_status(_stream_handle(cuda_stream)), "sr_noalloc_status")
 
 
 def make_pair_desc(left, right, disp, alpha0, alpha1, delta, wta=None) -> sr_pair_desc:

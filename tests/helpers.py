@@ -97,14 +97,15 @@ def kink_free_alpha(a0, a1, delta, H, h0, h1, step=0.0071):
     raise AssertionError("no kink-free alpha0 found")
 
 
-def near_flat_slack(warped, D, ncc_r, agg_r):
+def near_flat_slack(warped, D, ncc_r, agg_r, e=TOL_WARP):
     """Extra error allowed where a warped-target block is nearly flat.
 
     A cost of Eq. 3 is a centred dot product over n sigma_l sigma_r.  An
-    intensity error e <= TOL_WARP in the warped block (the bound asserted on
-    the warped image) moves the numerator by at most sqrt(n) sigma_l
-    sqrt(n) e (Cauchy-Schwarz) and sigma_r by at most e, so the cost moves by
-    at most 2 e / sigma_r: large where sigma_r is small but above the flat
+    intensity error e in the warped block (at most TOL_WARP, the bound
+    asserted on the warped image; a test may pass the error it measured)
+    moves the numerator by at most sqrt(n) sigma_l sqrt(n) e
+    (Cauchy-Schwarz) and sigma_r by at most e, so the cost moves by at most
+    2 e / sigma_r: large where sigma_r is small but above the flat
     threshold.  Returns (slack_l, slack_r) of shape [H][W][D] for the two
     cost volumes and their aggregates (the maximum over the bilateral
     window, since a weighted mean moves by no more than its largest term).
@@ -124,7 +125,7 @@ def near_flat_slack(warped, D, ncc_r, agg_r):
             s += blk
             s2 += blk * blk
     var = np.maximum(s2 / n - (s / n) ** 2, 0.0)
-    slack = np.where(var > 0, 2.0 * TOL_WARP / np.sqrt(np.maximum(var, 1e-300)), 0.0)
+    slack = np.where(var > 0, 2.0 * e / np.sqrt(np.maximum(var, 1e-300)), 0.0)
     slack = np.where(var < 0.8e-6, 0.0, slack)                 # flat on both sides: c = 0
     slack = np.where(np.abs(var - 1e-6) <= 0.2e-6, 2.0, slack)  # flatness may flip
     slack = np.minimum(slack, 2.0)

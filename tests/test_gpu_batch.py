@@ -1,6 +1,8 @@
 """Batched form: sr_match_batch over pairs of mixed sizes equals sr_match on
 each pair (same tile kernels, so the results are bit-identical), across graph
-replays, schedules chosen by the autotuner, and FP16 volumes."""
+replays, schedules chosen by the autotuner, and FP16 volumes; and each pair
+of a mixed-size batch agrees with the FP64 oracle at the tolerances of the
+single-pair parity tests."""
 import numpy as np
 import pytest
 
@@ -63,6 +65,50 @@ def _same(got, want):
         np.testing.assert_array_equal(np.isnan(gd), np.isnan(d))
         fin = np.isfinite(d)
         np.testing.assert_array_equal(gd[fin], d[fin])
+
+
+def _check_pair_against_oracle(left, right, a0, a1, dl, disp, wta):
+    """One pair of a batch against oracle.match (Eqs. 3, 8-12, Sec. II-C):
+    labels differ only at near-ties, the full disparity is within TOL_DSUB
+    where well conditioned, and validity (Eq. 11) is the oracle's wherever
+    the labels agree at the pixel and the target view is not a near-tie at
+    its match."""
+    import oracle
+    from helpers import AGREE_MIN, DEN_MIN, TAU_TIE, TOL_DSUB
+    H, W = left.shape
+    p = oracle.Params(W=W, H=H, D=D, ncc_r=NCC_R, agg_r=AGG_R, gamma_d=GD, gamma_r=GR,
+                      lr_thresh=1.0, alpha0=a0, alpha1=a1, delta=dl)
+    o = oracle.match(p, left, right, want=("lbl_l", "lbl_r", "gap_l", "gap_r", "den_l",
+                                           "valid", "dfull"))
+    diff = wta.astype(np.int64) != o.lbl_l
+    assert not np.any(diff & (o.gap_l >= TAU_TIE)), (W, H)
+    if W * H >= 5000:
+        assert 1.0 - diff.mean() >= AGREE_MIN
+    fin = np.isfinite(disp)
+    sharp = ~diff & (o.gap_l >= TAU_TIE) & (np.abs(o.den_l) >= DEN_MIN) & \
+        np.isfinite(o.dfull) & fin
+    if sharp.any():
+        assert np.abs(disp[sharp] - o.dfull[sharp]).max() <= TOL_DSUB
+    uu = np.arange(W)[None, :] - o.lbl_l
+    inb = uu >= 0
+    vv = np.broadcast_to(np.arange(H)[:, None], (H, W))
+    firm_match = np.ones((H, W), bool)
+    firm_match[inb] = o.gap_r[vv[inb], uu[inb]] >= TAU_TIE
+    firm = ~diff & firm_match
+    np.testing.assert_array_equal(fin[firm], o.valid.astype(bool)[firm])
+
+
+@pytest.mark.parametrize("variant", [0, 7])
+def test_batch_matches_the_oracle(variant):
+    """Every pair of a six-pair batch of mixed sizes (31x9 to 203x77) against
+    the oracle, for a persistent schedule and the per-pair schedule."""
+    from paper_1807_07433_gb300 import sr
+    pairs = _pairs(700)
+    with _ctx() as m:
+        sr.sr_set_batch_schedule(m.ctx, variant)
+        got = _batch(m.ctx, pairs)
+    for i, (left, right, a0, a1, dl) in enumerate(pairs):
+        _check_pair_against_oracle(left, right, a0, a1, dl, *got[i])
 
 
 def _ctx(vt=0):

@@ -1,8 +1,14 @@
 """GPU road-plane fitting (sr_fit_alpha, sr_fit_roll; Sec. II-A) against the
-oracle on the same disparity maps: inlier counts, the winning hypothesis and
-the pixel count are integers and must match exactly (both sides decide in
-single precision with one fused multiply-add); the least-squares results are
-FP64 sums in different orders (relative 1e-10)."""
+oracle on the same disparity maps.  The oracle decides inliers by the
+definition |d - (a0 + a1 v)| <= tau in double precision; the GPU decides in
+single precision (the model rounded to float, one fused multiply-add).  The
+two may therefore differ only at pixels whose double-precision residual lies
+within the float evaluation's rounding bound of tau ("borderline" pixels):
+inlier counts must agree up to each hypothesis' borderline pixels, whose
+number is reported; the winning hypothesis and the least-squares line (FP64
+sums in different orders: relative 1e-10) must agree wherever the borderline
+pixels cannot change them.  The roll fit uses no threshold and is compared
+at 1e-10."""
 import numpy as np
 import pytest
 
@@ -26,15 +32,81 @@ def _matcher(W, H, w=None):
                       stream=torch.cuda.current_stream())
 
 
+U32 = 2.0 ** -24
+
+
+def _borderline(disp_np, pairs):
+    """Per hypothesis (None without a model): the pixels whose FP64 residual
+    |d - (a0 + a1 v)| is within the single-precision evaluation's rounding
+    bound of TAU, 4u (|a0| + |a1| v + |d|); the FP64 line (a0, a1)."""
+    H, W = disp_np.shape
+    flat = disp_np.ravel().astype(np.float64)
+    vv = np.repeat(np.arange(H), W).astype(np.float64)
+    out = []
+    for i1, i2 in pairs:
+        if not (0 <= i1 < H * W and 0 <= i2 < H * W) or i1 // W == i2 // W or \
+                np.isnan(flat[i1]) or np.isnan(flat[i2]):
+            out.append(None)
+            continue
+        a1 = (flat[i2] - flat[i1]) / float(i2 // W - i1 // W)
+        a0 = flat[i1] - a1 * float(i1 // W)
+        res = np.abs(flat - (a0 + a1 * vv))
+        eps = 4.0 * U32 * (abs(a0) + abs(a1) * vv + np.abs(flat))
+        out.append((np.isfinite(flat) & (np.abs(res - TAU) <= eps), a0, a1))
+    return out
+
+
 def _check_alpha(m, disp_np, pairs):
     import torch
     from paper_1807_07433_gb300 import sr
     got = sr.sr_fit_alpha(m.ctx, torch.from_numpy(disp_np).cuda(), pairs, TAU)
     want = oracle.fit_alpha(disp_np, pairs, TAU)
-    np.testing.assert_array_equal(got["counts"], want.counts)
-    assert got["best"] == want.best and got["n_inliers"] == want.n_inliers
-    np.testing.assert_allclose(got["alpha"], want.alpha, rtol=1e-10, atol=1e-12)
+    border = _borderline(disp_np, pairs)
+    nb = np.array([-1 if b is None else int(b[0].sum()) for b in border])
+    print(f"borderline pixels: {int(nb[nb > 0].sum())} over {int((nb > 0).sum())} of "
+          f"{len(pairs)} hypotheses")
+    np.testing.assert_array_equal(got["counts"] < 0, want.counts < 0)
+    has = want.counts >= 0
+    assert np.all(np.abs(got["counts"][has] - want.counts[has]) <= nb[has])
+    if got["best"] != want.best:
+        # only borderline pixels can reorder hypotheses
+        gb, wb = got["best"], want.best
+        assert want.counts[gb] + nb[gb] + nb[wb] >= want.counts[wb]
+        return got
+    b = want.best
+    if nb[b] == 0:
+        assert got["n_inliers"] == want.n_inliers
+        np.testing.assert_allclose(got["alpha"], want.alpha, rtol=1e-10, atol=1e-12)
+    else:   # the two inlier sets differ by borderline pixels only
+        assert abs(got["n_inliers"] - want.n_inliers) <= nb[b]
+        np.testing.assert_allclose(got["alpha"], want.alpha, rtol=0,
+                                   atol=2.0 * TAU * nb[b] / max(want.n_inliers, 1) + 1e-9)
     return got
+
+
+def test_borderline_residuals_on_the_gpu():
+    """Pixels a few float ulps either side of the threshold on the line
+    through (v=0, d=1) and (v=3, d=2): the GPU's count differs from the
+    oracle's by no more than the borderline pixels (here, all but two)."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    H, W = 64, 9
+    d = np.empty((H, W), np.float32)
+    for v in range(H):
+        x = np.float32(1.0 + v / 3.0 + TAU)
+        for k, step in enumerate(range(-4, 5)):
+            y = x
+            for _ in range(abs(step)):
+                y = np.nextafter(y, np.float32(np.inf if step > 0 else -np.inf))
+            d[v, k] = y
+    d[0, 0], d[3, 0] = 1.0, 2.0
+    pairs = np.array([[0, 3 * W]], np.int32)
+    with _matcher(W, H) as m:
+        got = sr.sr_fit_alpha(m.ctx, torch.from_numpy(d).cuda(), pairs, TAU)
+    want = oracle.fit_alpha(d, pairs, TAU)
+    nb = int(_borderline(d, pairs)[0][0].sum())
+    assert nb >= H * W - 2 - 2 * H
+    assert abs(int(got["counts"][0]) - int(want.counts[0])) <= nb
 
 
 @pytest.fixture(scope="module")

@@ -107,18 +107,31 @@ def test_reconstruct_matches_closed_form(w):
 
 
 def test_two_volume_identity_on_gpu():
-    """Sec. II-B-1: the target volume at (u-d,v,d) equals the reference volume
-    at (u,v,d); the GPU computes the two independently."""
+    """Sec. II-B-1: the target volume at (u, v, d) equals the reference
+    volume at (u + d, v, d).  sr_match_restricted computes the two volumes in
+    separate NCC passes (the reference-view and the target-view kernel); with
+    a radius of D - 1 every pixel searches all disparities, so both volumes
+    are complete.  (sr_match stores only the extended reference volume and
+    reads the target view from it, where the identity holds by
+    construction.)  Both volumes are also checked against the oracle."""
+    import torch
     from paper_1807_07433_gb300 import sr
     w = CASES[1]
     left, right, _ = synth.make_pair(w.scene)
-    g = run_gpu(w, left, right, buffers=(("cost_l", sr.SR_BUF_COST_L),
-                                         ("cost_r", sr.SR_BUF_COST_R)))
-    W = left.shape[1]
+    H, W = left.shape
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        m.match_restricted(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(),
+                           w.D - 1)
+        torch.cuda.synchronize()
+        cl, cr = m.buffer(sr.SR_BUF_COST_L), m.buffer(sr.SR_BUF_COST_R)
     for d in range(w.D):
-        np.testing.assert_allclose(g["cost_r"][:, :W - d, d], g["cost_l"][:, d:, d], rtol=0,
-                                   atol=2 * TOL_COST)
-    assert np.abs(g["cost_l"]).max() <= 1.0 + 1e-5
+        np.testing.assert_allclose(cr[:, :W - d, d], cl[:, d:, d], rtol=0, atol=2 * TOL_COST)
+    assert np.abs(cl).max() <= 1.0 + 1e-5
+    o = run_oracle(w, left, right, ("cost_l", "cost_r"))
+    np.testing.assert_allclose(cl, o.cost_l, rtol=0, atol=TOL_COST)
+    np.testing.assert_allclose(cr, o.cost_r, rtol=0, atol=TOL_COST)
 
 
 @pytest.mark.parametrize("w", [synth.C2, synth.C3], ids=lambda w: w.name)

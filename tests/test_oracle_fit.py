@@ -2,11 +2,13 @@
 least squares with RANSAC over point pairs of a disparity map, and the roll
 angle from a plane fitted to a near-field patch.
 
-The pins use data without borderline residuals (every pixel is either on
-the model up to float rounding or at least 3 px away), so brute-force
-inlier counts in float64 must equal the oracle's single-precision
-decisions, and the least-squares results are checked against
-numpy.linalg.lstsq on the same inlier set."""
+The inlier test is the definition |d - (a0 + a1 v)| <= tau in double
+precision.  Most pins use data without borderline residuals (every pixel is
+either on the model up to float rounding or at least 3 px away); one pin
+places pixels a float ulp or two either side of the boundary, where a
+single-precision evaluation of the same test decides differently, and
+checks the oracle against float64 brute force there.  The least-squares
+results are checked against numpy.linalg.lstsq on the same inlier set."""
 import math
 
 import numpy as np
@@ -58,6 +60,46 @@ def test_counts_equal_brute_force_and_best_is_the_true_line():
     ref = np.linalg.lstsq(A, d[inl].astype(np.float64), rcond=None)[0]
     np.testing.assert_allclose(fit.alpha, ref, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(fit.alpha, [21.5, 0.0731], rtol=0, atol=2e-6)
+
+
+def _float_inlier_count(flat, vv, a0, a1, tau):
+    """The inlier test evaluated in single precision with one fused
+    multiply-add (a1 v + a0 is exact in float64 for float a0, a1 and
+    small integer v, so rounding it once to float32 is the fma)."""
+    a0f, a1f = np.float32(a0), np.float32(a1)
+    m = (np.float64(a1f) * vv + np.float64(a0f)).astype(np.float32)
+    r = np.abs(flat.astype(np.float32) - m)
+    return int(np.sum(r <= np.float32(tau)))
+
+
+def test_borderline_residuals_follow_the_double_precision_definition():
+    """Pixels within a float ulp or two of |d - (a0 + a1 v)| = tau, on the
+    line through (v=0, d=1) and (v=3, d=2) (a1 = 1/3, not a float): the
+    oracle's counts equal float64 brute force, and the data is chosen so
+    that the single-precision test counts differently."""
+    H, W = 64, 9
+    d = np.empty((H, W), np.float32)
+    vv = np.repeat(np.arange(H), W).astype(np.float64)
+    for v in range(H):
+        x = np.float32(1.0 + v / 3.0 + TAU)
+        for k, step in enumerate(range(-4, 5)):       # x and 4 floats either side
+            y = x
+            for _ in range(abs(step)):
+                y = np.nextafter(y, np.float32(np.inf if step > 0 else -np.inf))
+            d[v, k] = y
+    d[0, 0], d[3, 0] = 1.0, 2.0                       # the hypothesis' two points
+    pairs = np.array([[0, 3 * W]], np.int32)
+    fit = oracle.fit_alpha(d, pairs, TAU)
+    flat = d.ravel().astype(np.float64)
+    a1 = (2.0 - 1.0) / 3.0
+    a0 = 1.0 - a1 * 0.0
+    want = int(np.sum(np.abs(flat - (a0 + a1 * vv)) <= TAU))
+    assert fit.counts[0] == want
+    assert _float_inlier_count(flat, vv, a0, a1, TAU) != want
+    inl = np.abs(flat - (a0 + a1 * vv)) <= TAU
+    A = np.stack([np.ones(inl.sum()), vv[inl]], 1)
+    ref = np.linalg.lstsq(A, flat[inl], rcond=None)[0]
+    np.testing.assert_allclose(fit.alpha, ref, rtol=1e-12, atol=1e-12)
 
 
 def test_no_model_at_all():
