@@ -125,6 +125,33 @@ sr_status sr_set_camera(sr_ctx *ctx, double f_px, double baseline, double u0, do
 sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                    float *d_disp, int16_t *d_wta_or_null);
 
+/* One band of rows of sr_match's result: the disparities of image rows
+ * [y0, y1) of the W x H frame the context was created for, equal bit for bit
+ * to those rows of sr_match on the whole frame.  Every step of the path is
+ * row-local up to a window: an NCC block (Eq. 3) reaches ncc_radius rows and
+ * a bilateral window (Eq. 8) agg_radius rows, so a band needs only the halo
+ * rows r0 = max(0, y0 - h) .. r1 - 1 = min(H, y1 + h) - 1, h = ncc_radius +
+ * agg_radius, of both images; it takes the plane of its rows in the frame
+ * (row v shifted by alpha0 + alpha1*v - delta, v counted from the frame's
+ * first row).  This is the row partition of a frame over several GPUs: each
+ * holds its band and halo rows, and the bands need no exchange.
+ *   d_left_rows, d_right_rows  image rows r0..r1-1 (pointers to row r0),
+ *                              row pitch pitch_bytes (>= W)
+ *   y0, y1                     0 <= y0 < y1 <= H
+ *   d_disp_rows                (y1 - y0) x W floats, dense: rows y0..y1-1
+ *                              of sr_match's d_disp
+ *   d_wta_rows_or_null         optional (y1 - y0) x W int16: the same rows
+ *                              of sr_match's d_wta_or_null
+ * The halo rows are matched too (and discarded), so a band costs its rows
+ * plus up to 2h rows.  Uses the context's scratch (sr_get_buffer reports
+ * SR_ERR_STATE afterwards); the first call allocates 6*W*H bytes of band
+ * output and builds a tensor map for bands of r1 - r0 rows (rebuilt when
+ * that count changes).  Asynchronous.  Errors: SR_ERR_INVALID_ARG,
+ * SR_ERR_OOM, SR_ERR_CUDA. */
+sr_status sr_match_rows(sr_ctx *ctx, const uint8_t *d_left_rows, const uint8_t *d_right_rows,
+                        int pitch_bytes, int y0, int y1, float *d_disp_rows,
+                        int16_t *d_wta_rows_or_null);
+
 /* Restricted search: sr_match with every pixel of both views searching only
  * the window [c - radius, c + radius] (clamped to 0..D-1) around its centre
  * c, the plan of the paper's Sec. IV (filter only the space around previously
@@ -184,7 +211,8 @@ sr_status sr_match_host_async(sr_ctx *ctx, const uint8_t *h_left, const uint8_t 
  * values sr_match writes.
  *   Size limit: with A(b) = b rounded up to a multiple of 256 and e the
  *   bytes of one stored cost (4 for SR_VOL_F32, 2 for SR_VOL_F16/BF16),
- *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + A(e*H*(W+D-1)*D) + 2*A(2*W*H) <= 32 MiB
+ *     2*A(4*W*H) + 4*A(4*H*(W+D-1)) + A(e*H*(W+D-1)*D) + 2*A(2*W*H) + A(8*H)
+ *       <= 32 MiB
  *   (e.g. 640x480 at D = 16, 400x225 at D = 64 with FP32 volumes); larger
  *   frames are rejected with SR_ERR_UNSUPPORTED before any GPU work.
  *   The first call in a CUDA context (the device's primary context, or a

@@ -490,8 +490,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
                 if (ur >= 0)
                     ok = fabsf((float)(l - (int)win.post.lbl_r[(size_t)v * W + ur])) <=
                          win.post.lr_thresh;
-                const double sv = win.post.alpha0 + win.post.alpha1 * (double)v - win.post.delta;
-                win.post.disp[o] = ok ? (float)((double)ds + sv) : __int_as_float(0x7fc00000);
+                win.post.disp[o] = ok ? post_disp(ds, win.post.rowsh[v]) : __int_as_float(0x7fc00000);
                 if (win.post.wta) win.post.wta[o] = (int16_t)l;
             }
         }

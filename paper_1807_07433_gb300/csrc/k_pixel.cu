@@ -15,8 +15,8 @@ constexpr int kBX = kPixTX, kBY = kPixTY;
 __device__ __forceinline__ void warp_px(const uint8_t *__restrict__ right, int pitch, int W,
                                         double alpha0, double alpha1, double delta,
                                         float *__restrict__ rw, int x, int v) {
-    // s(v) of Sec. II-A in double: it also feeds Sec. II-C post-processing.
-    const double s = alpha0 + alpha1 * (double)v - delta;
+    // s(v) of Sec. II-A, evaluated per pixel here (the batched form)
+    const double s = row_shift(alpha0, alpha1, delta, v);
     double k = floor(s);
     const float w = (float)(s - k);
     k = fmin(fmax(k, -2.0 * W - 2.0), 2.0 * W + 2.0);   // beyond this every read clamps
@@ -116,17 +116,15 @@ __global__ void k_stats_right(const float *__restrict__ rw, int W, int H, int D,
 
 __device__ __forceinline__ void lrc_px(const int16_t *__restrict__ lbl_l,
                                        const int16_t *__restrict__ lbl_r,
-                                       const float *__restrict__ dsub, int W, double alpha0,
-                                       double alpha1, double delta, float lr_thresh,
-                                       float *__restrict__ disp, int16_t *__restrict__ wta_out,
-                                       int u, int v) {
+                                       const float *__restrict__ dsub, int W, float2 sh,
+                                       float lr_thresh, float *__restrict__ disp,
+                                       int16_t *__restrict__ wta_out, int u, int v) {
     const size_t i = (size_t)v * W + u;
     const int l = lbl_l[i];
     const int ur = u - l;
     bool ok = false;
     if (ur >= 0) ok = fabsf((float)(l - (int)lbl_r[(size_t)v * W + ur])) <= lr_thresh;
-    const double s = alpha0 + alpha1 * (double)v - delta;
-    disp[i] = ok ? (float)((double)dsub[i] + s) : __int_as_float(0x7fc00000);
+    disp[i] = ok ? post_disp(dsub[i], sh) : __int_as_float(0x7fc00000);
     if (wta_out) wta_out[i] = (int16_t)l;
 }
 
@@ -136,16 +134,17 @@ __device__ __forceinline__ void lrc_px(const int16_t *__restrict__ lbl_l,
 constexpr int kLrcPX = 4;
 
 __global__ void k_lrc_post(const int16_t *__restrict__ lbl_l, const int16_t *__restrict__ lbl_r,
-                           const float *__restrict__ dsub, int W, int H, double alpha0,
-                           double alpha1, double delta, float lr_thresh, float *__restrict__ disp,
-                           int16_t *__restrict__ wta_out) {
+                           const float *__restrict__ dsub, int W, int H,
+                           const float2 *__restrict__ rowsh, float lr_thresh,
+                           float *__restrict__ disp, int16_t *__restrict__ wta_out) {
     const int u0 = blockIdx.x * kBX * kLrcPX + threadIdx.x;
     const int v = blockIdx.y * kBY + threadIdx.y;
     if (v >= H) return;
+    const float2 sh = rowsh[v];
 #pragma unroll
     for (int i = 0; i < kLrcPX; ++i) {
         const int u = u0 + i * kBX;
-        if (u < W) lrc_px(lbl_l, lbl_r, dsub, W, alpha0, alpha1, delta, lr_thresh, disp, wta_out, u, v);
+        if (u < W) lrc_px(lbl_l, lbl_r, dsub, W, sh, lr_thresh, disp, wta_out, u, v);
     }
 }
 
@@ -173,8 +172,10 @@ __global__ void k_warp_batch(const PairDesc *__restrict__ pairs, const int *__re
     for (int t = blockIdx.x; t < st[n]; t += gridDim.x) {
         const PairDesc *P;
         int x, v;
-        if (batch_pixel(pairs, st, n, t, 0, &P, &x, &v, &pp))
+        if (batch_pixel(pairs, st, n, t, 0, &P, &x, &v, &pp)) {
             warp_px(P->right, P->pitch, P->W, P->alpha0, P->alpha1, P->delta, P->rw, x, v);
+            if (x == 0) P->rowsh[v] = split_shift(row_shift(P->alpha0, P->alpha1, P->delta, v));
+        }
     }
 }
 
@@ -204,8 +205,8 @@ __global__ void k_lrc_post_batch(const PairDesc *__restrict__ pairs, const int *
         const PairDesc *P;
         int x, v;
         if (batch_pixel(pairs, st, n, t, 0, &P, &x, &v, &pp))
-            lrc_px(P->lbl_l, P->lbl_r, P->dsub, P->W, P->alpha0, P->alpha1, P->delta, lr_thresh,
-                   P->disp, P->wta, x, v);
+            lrc_px(P->lbl_l, P->lbl_r, P->dsub, P->W, P->rowsh[v], lr_thresh, P->disp, P->wta,
+                   x, v);
     }
 }
 
@@ -244,9 +245,9 @@ dim3 grid_for(int w, int h) { return dim3((w + kBX - 1) / kBX, (h + kBY - 1) / k
 template <int RN>
 __global__ void __launch_bounds__(kBX * kBY)
 k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch, int W,
-       int H, int D, double alpha0, double alpha1, double delta, float *__restrict__ rw,
-       float *__restrict__ mu_l, float *__restrict__ inv_l, float *__restrict__ mu_r,
-       float *__restrict__ inv_r) {
+       int H, int D, double alpha0, double alpha1, double delta, int row0,
+       float *__restrict__ rw, float *__restrict__ mu_l, float *__restrict__ inv_l,
+       float *__restrict__ mu_r, float *__restrict__ inv_r, float2 *__restrict__ rowsh) {
     constexpr int B = 2 * RN + 1, TH = kBY + 2 * RN, TW = kBX + 2 * RN;
     constexpr int n = B * B;
     __shared__ int s_l[TH][TW];           // left intensities
@@ -261,7 +262,9 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     const int xr0 = x0 - (D - 1);         // first target-block centre of the tile
     if (tid < TH) {
         const int y = clampi(y0 - RN + tid, 0, H - 1);
-        const double sh = alpha0 + alpha1 * (double)y - delta;
+        const double sh = row_shift(alpha0, alpha1, delta, y + row0);
+        if (blockIdx.x == 0 && tid >= RN && tid < RN + kBY && y0 - RN + tid < H)
+            rowsh[y0 - RN + tid] = split_shift(sh);   // one column of tiles writes each row
         double k = floor(sh);
         s_w[tid] = (float)(sh - k);
         k = fmin(fmax(k, -2.0 * W - 2.0), 2.0 * W + 2.0);   // beyond this every read clamps
@@ -354,14 +357,15 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
 }  // namespace
 
 cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, int W, int H, int D,
-                        int ncc_r, double alpha0, double alpha1, double delta, float *rw,
-                        float *mu_l, float *inv_l, float *mu_r, float *inv_r, cudaStream_t st) {
+                        int ncc_r, double alpha0, double alpha1, double delta, int row0,
+                        float *rw, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
+                        float2 *rowsh, cudaStream_t st) {
     const dim3 grid = grid_for(W + D - 1, H), block(kBX, kBY);
     switch (ncc_r) {
 #define SR_PREP(RN_)                                                                          \
     case RN_:                                                                                 \
         k_prep<RN_><<<grid, block, 0, st>>>(left, right, pitch, W, H, D, alpha0, alpha1, delta, \
-                                            rw, mu_l, inv_l, mu_r, inv_r);                     \
+                                            row0, rw, mu_l, inv_l, mu_r, inv_r, rowsh);        \
         break;
         SR_PREP(1) SR_PREP(2) SR_PREP(3) SR_PREP(4) SR_PREP(5)
 #undef SR_PREP
@@ -399,10 +403,10 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
 }
 
 cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,
-                            int H, double alpha0, double alpha1, double delta, float lr_thresh,
-                            float *disp, int16_t *wta_out, cudaStream_t st) {
+                            int H, const float2 *rowsh, float lr_thresh, float *disp,
+                            int16_t *wta_out, cudaStream_t st) {
     k_lrc_post<<<grid_for(ceil_div(W, kLrcPX), H), dim3(kBX, kBY), 0, st>>>(
-        lbl_l, lbl_r, dsub, W, H, alpha0, alpha1, delta, lr_thresh, disp, wta_out);
+        lbl_l, lbl_r, dsub, W, H, rowsh, lr_thresh, disp, wta_out);
     return cudaGetLastError();
 }
 

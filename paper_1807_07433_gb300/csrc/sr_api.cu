@@ -247,6 +247,7 @@ cudaError_t dalloc(T **p, size_t n) {
 
 void free_all(sr_ctx *c) {
     void *ptrs[] = {c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, c->vol_l, c->vol_r, c->dsub,
+                    c->rowsh, c->band_disp, c->band_wta,
                     c->lbl_l, c->lbl_r, c->agg_l, c->agg_r, c->stage_l, c->stage_r,
                     c->stage_disp, c->d_err, c->g_vol, c->g_wsum, c->g_rw, c->g_partial,
                     c->f_pairs, c->f_has, c->f_counts, c->f_model, c->f_partial, c->band,
@@ -418,6 +419,7 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->vol_l, H * WE * D * sr::vol_elem_bytes(p.vol_dtype));
     if (e == cudaSuccess) e = cudaMalloc(&c->vol_r, vbytes);
     if (e == cudaSuccess) e = dalloc(&c->dsub, npx);
+    if (e == cudaSuccess) e = dalloc(&c->rowsh, H);
     if (e == cudaSuccess) e = dalloc(&c->lbl_l, npx);
     if (e == cudaSuccess) e = dalloc(&c->lbl_r, npx);
     if (e == cudaSuccess) e = dalloc(&c->d_err, 1);
@@ -522,7 +524,8 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     const int WE = W + D - 1;
     SR_TRY(c, mark(), "cudaEventRecord");
     SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
-                              c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
+                              c->alpha1, c->delta, 0, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                              c->inv_r, c->rowsh, st),
            "prep");
     SR_TRY(c, mark(), "cudaEventRecord");
     // one extended reference volume holds both views (target c(u,d) =
@@ -544,9 +547,7 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     post.post.lbl_r = c->lbl_r;
     post.post.disp = d_disp;
     post.post.wta = d_wta_or_null;
-    post.post.alpha0 = c->alpha0;
-    post.post.alpha1 = c->alpha1;
-    post.post.delta = c->delta;
+    post.post.rowsh = c->rowsh;
     post.post.lr_thresh = p.lr_thresh;
     SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
                              p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
@@ -557,6 +558,69 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     c->vol_ext = true;
     c->agg_valid = keep;
     c->timed = prof;
+    return SR_OK;
+}
+
+sr_status sr_match_rows(sr_ctx *c, const uint8_t *d_left_rows, const uint8_t *d_right_rows,
+                        int pitch_bytes, int y0, int y1, float *d_disp_rows,
+                        int16_t *d_wta_rows_or_null) {
+    if (!c || !d_left_rows || !d_right_rows || !d_disp_rows || pitch_bytes < c->p.width)
+        return SR_ERR_INVALID_ARG;
+    const sr_params &p = c->p;
+    const int W = p.width, H = p.height, D = p.max_disp;
+    if (y0 < 0 || y1 > H || y0 >= y1) return SR_ERR_INVALID_ARG;
+    // the band and the halo rows its NCC blocks and bilateral windows reach
+    const int halo = p.ncc_radius + p.agg_radius;
+    const int r0 = std::max(0, y0 - halo), r1 = std::min(H, y1 + halo), Hs = r1 - r0;
+    const size_t npx = (size_t)W * H;
+    cudaStream_t st = c->st;
+    if (!c->band_disp) {
+        SR_TRY(c, dalloc(&c->band_disp, npx), "cudaMalloc(band disparity)");
+        SR_TRY(c, dalloc(&c->band_wta, npx), "cudaMalloc(band labels)");
+    }
+    if (c->band_rows != Hs) {
+        // the sheared view of a volume of Hs rows: copies past its last row
+        // read zeros, as for a whole frame
+        if (!sr::encode_shear_map(&c->tmap_band, c->vol_l, p.vol_dtype, W, Hs, D, p.agg_radius)) {
+            snprintf(c->err, sizeof(c->err), "cuTensorMapEncodeTiled failed or is unavailable");
+            c->band_rows = 0;
+            return SR_ERR_CUDA;
+        }
+        c->band_rows = Hs;
+    }
+    c->matched = false;   // the scratch holds a band, not a frame
+    c->timed = false;
+    const int WE = W + D - 1;
+    SR_TRY(c, sr::launch_prep(d_left_rows, d_right_rows, pitch_bytes, W, Hs, D, p.ncc_radius,
+                              c->alpha0, c->alpha1, c->delta, r0, c->rw, c->mu_l, c->inv_l,
+                              c->mu_r, c->inv_r, c->rowsh, st),
+           "prep");
+    SR_TRY(c, sr::launch_ncc(false, d_left_rows, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                             c->inv_r, W, Hs, D, p.ncc_radius, c->vol_l, p.vol_dtype, st, nullptr,
+                             WE),
+           "ncc");
+    const sr::AggDebug dbg = agg_debug(c);
+    SR_TRY(c, sr::launch_agg_shear(&c->tmap_band, p.vol_dtype, c->rw, W, Hs, D, p.agg_radius,
+                                   p.gamma_d, p.gamma_r, c->lbl_r, nullptr, dbg, st),
+           "agg_tgt");
+    sr::AggWin post;
+    post.post.lbl_r = c->lbl_r;
+    post.post.disp = c->band_disp;
+    post.post.wta = c->band_wta;
+    post.post.rowsh = c->rowsh;
+    post.post.lr_thresh = p.lr_thresh;
+    SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left_rows, pitch_bytes, nullptr, W, Hs, D,
+                             p.agg_radius, p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, nullptr, dbg,
+                             st, post, WE),
+           "agg_ref");
+    const size_t off = (size_t)(y0 - r0) * W, n = (size_t)(y1 - y0) * W;
+    SR_TRY(c, cudaMemcpyAsync(d_disp_rows, c->band_disp + off, n * sizeof(float),
+                              cudaMemcpyDeviceToDevice, st),
+           "band rows");
+    if (d_wta_rows_or_null)
+        SR_TRY(c, cudaMemcpyAsync(d_wta_rows_or_null, c->band_wta + off, n * sizeof(int16_t),
+                                  cudaMemcpyDeviceToDevice, st),
+               "band rows");
     return SR_OK;
 }
 
@@ -606,7 +670,8 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
     c->timed = false;
     const sr::AggDebug dbg = agg_debug(c);
     SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
-                              c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
+                              c->alpha1, c->delta, 0, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                              c->inv_r, c->rowsh, st),
            "prep");
     const int2 *nrange = banded ? c->nrange : nullptr;
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
@@ -632,8 +697,8 @@ sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d
     SR_TRY(c, sr::launch_agg(c->vol_r, p.vol_dtype, nullptr, 0, c->rw, W, H, D, p.agg_radius,
                              p.gamma_d, p.gamma_r, c->lbl_r, nullptr, nullptr, dbg, st, win),
            "agg_tgt");
-    SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->alpha0, c->alpha1,
-                                  c->delta, p.lr_thresh, d_disp, d_wta_or_null, st),
+    SR_TRY(c, sr::launch_lrc_post(c->lbl_l, c->lbl_r, c->dsub, W, H, c->rowsh, p.lr_thresh,
+                                  d_disp, d_wta_or_null, st),
            "lrc_post");
     c->matched = true;
     c->vol_ext = false;
@@ -747,7 +812,8 @@ sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right
     cudaStream_t st = c->st;
     c->matched = false;   // the context's scratch no longer holds the last sr_match
     SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
-                              c->alpha1, c->delta, c->rw, c->mu_l, c->inv_l, c->mu_r, c->inv_r, st),
+                              c->alpha1, c->delta, 0, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                              c->inv_r, c->rowsh, st),
            "prep");
     SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
                              c->inv_r, W, H, D, p.ncc_radius, cost, sr::kVolF32, st),

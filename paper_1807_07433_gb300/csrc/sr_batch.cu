@@ -120,7 +120,7 @@ size_t pair_scratch_bytes(const sr_params &p, int W, int H) {
     // vol_l holds the extended reference volume [H][WE][D] (schedule C) or the
     // reference volume [H][W][D] (persistent schedules, a prefix of it)
     return 2 * a256(npx * 4) + 4 * a256((size_t)H * WE * 4) + a256((size_t)H * WE * p.max_disp * e) +
-           a256(npx * p.max_disp * e) + 2 * a256(npx * 2);
+           a256(npx * p.max_disp * e) + 2 * a256(npx * 2) + a256((size_t)H * 8);
 }
 
 std::string tune_key(const sr_ctx *c, int n, const sr_pair_desc *pairs) {
@@ -222,7 +222,8 @@ cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     const sr::AggDebug dbg = agg_debug(c);
     cudaError_t e;
     if ((e = sr::launch_prep(P.left, P.right, P.pitch, P.W, P.H, D, p.ncc_radius, P.alpha0,
-                             P.alpha1, P.delta, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, st)) != cudaSuccess) return e;
+                             P.alpha1, P.delta, 0, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r,
+                             P.rowsh, st)) != cudaSuccess) return e;
     // one extended reference volume for both views, as in sr_match
     const int WE = P.W + D - 1;
     if ((e = sr::launch_ncc(false, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
@@ -235,9 +236,7 @@ cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     post.post.lbl_r = P.lbl_r;
     post.post.disp = P.disp;
     post.post.wta = P.wta;
-    post.post.alpha0 = P.alpha0;
-    post.post.alpha1 = P.alpha1;
-    post.post.delta = P.delta;
+    post.post.rowsh = P.rowsh;
     post.post.lr_thresh = p.lr_thresh;
     return sr::launch_agg(P.vol_l, p.vol_dtype, P.left, P.pitch, nullptr, P.W, P.H, D,
                           p.agg_radius, p.gamma_d, p.gamma_r, P.lbl_l, P.dsub, nullptr, dbg, st,
@@ -329,6 +328,7 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
         o.vol_r = take(npx * D * sr::vol_elem_bytes(p.vol_dtype));
         o.lbl_l = reinterpret_cast<int16_t *>(take(npx * 2));
         o.lbl_r = reinterpret_cast<int16_t *>(take(npx * 2));
+        o.rowsh = reinterpret_cast<float2 *>(take((size_t)H * 8));
         if (!sr::encode_shear_map(&b->tmaps[k], o.vol_l, p.vol_dtype, W, H, D, p.agg_radius))
             return cudaErrorNotSupported;
         b->tiles_pix[k] = sr::ceil_div(W, sr::kPixTX) * sr::ceil_div(H, sr::kPixTY);

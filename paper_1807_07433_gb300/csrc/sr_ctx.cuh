@@ -30,6 +30,14 @@ struct sr_ctx {
     CUtensorMap tmap_x{};            // sheared view of vol_l (launch_agg_shear)
     bool tmap_x_ok = false;
     float *dsub = nullptr;
+    float2 *rowsh = nullptr;         // [H] split row shifts of the last prep
+    // sr_match_rows: full-disparity and label maps of the last band with its
+    // halo rows (on first use, W*H each), and the sheared view of vol_l for
+    // a band of band_rows image rows
+    float *band_disp = nullptr;
+    int16_t *band_wta = nullptr;
+    CUtensorMap tmap_band{};
+    int band_rows = 0;
     int16_t *lbl_l = nullptr, *lbl_r = nullptr;
     float *agg_l = nullptr, *agg_r = nullptr;
     // host-buffer staging: slot 0 for sr_match_host; slots 0 and 1 for

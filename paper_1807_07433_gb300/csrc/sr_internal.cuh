@@ -51,6 +51,24 @@ __device__ __forceinline__ void store8(__nv_bfloat16 *p, const float *v) {
     *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(h);
 }
 
+// Sec. II-A row shift of image row v, s(v) = alpha0 + alpha1 v - delta: the
+// plane of Eq. 2, evaluated once per image row in FP64 (a row's shift enters
+// the warp as its integer part and fraction, and the post-processing of Sec.
+// II-C adds it back).
+__host__ __device__ __forceinline__ double row_shift(double alpha0, double alpha1, double delta,
+                                                     int v) {
+    return alpha0 + alpha1 * (double)v - delta;
+}
+// s split into two floats, hi = s rounded to float and lo = the rest rounded
+// to float, so that the per-pixel post-processing runs in FP32.
+__device__ __forceinline__ float2 split_shift(double s) {
+    const float hi = __double2float_rn(s);
+    return make_float2(hi, __double2float_rn(s - (double)hi));
+}
+// Sec. II-C: full disparity = subpixel residual disparity + s(v), from the
+// split shift of the pixel's row.
+__device__ __forceinline__ float post_disp(float ds, float2 sh) { return (ds + sh.x) + sh.y; }
+
 // Supported compile-time parameter sets.
 bool ncc_supported(int D, int ncc_r);
 bool agg_supported(int D, int agg_r);
@@ -70,10 +88,14 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
                          cudaStream_t st);
 
 // launch_warp and launch_stats in one kernel (the same values): the warped
-// image rw and the four statistics arrays.
+// image rw and the four statistics arrays, and the split row shift
+// rowsh[v] = split_shift(s(v + row0)) of every row (for the post-processing).
+// row0: image row of the first row of left/right; the rows of a band of a
+// larger frame take the plane of their rows in that frame.
 cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, int W, int H, int D,
-                        int ncc_r, double alpha0, double alpha1, double delta, float *rw,
-                        float *mu_l, float *inv_l, float *mu_r, float *inv_r, cudaStream_t st);
+                        int ncc_r, double alpha0, double alpha1, double delta, int row0,
+                        float *rw, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
+                        float2 *rowsh, cudaStream_t st);
 
 // Eq. 3 cost volume [H][Wo][D], stored as vt (VolType; FP32 arithmetic,
 // rounded to nearest on store).  target = false: reference volume
@@ -113,7 +135,7 @@ struct AggPost {
     const int16_t *lbl_r = nullptr;
     float *disp = nullptr;           // full disparity, NaN where rejected
     int16_t *wta = nullptr;          // optional copy of the reference labels
-    double alpha0 = 0.0, alpha1 = 0.0, delta = 0.0;
+    const float2 *rowsh = nullptr;   // split row shift per row (launch_prep)
     float lr_thresh = 0.0f;
 };
 struct AggWin {
@@ -172,10 +194,11 @@ cudaError_t launch_tile_bands(const AggWin &win, int W, int H, int align, int *b
 cudaError_t launch_ncc_ranges(const int *band, int W, int H, int D, int agg_r, int2 *range,
                               cudaStream_t st);
 
-// Eq. 11 check with tolerance, then Sec. II-C post-processing.
+// Eq. 11 check with tolerance, then Sec. II-C post-processing with the split
+// row shifts rowsh [H] of launch_prep.
 cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,
-                            int H, double alpha0, double alpha1, double delta, float lr_thresh,
-                            float *disp, int16_t *wta_out, cudaStream_t st);
+                            int H, const float2 *rowsh, float lr_thresh, float *disp,
+                            int16_t *wta_out, cudaStream_t st);
 
 // Sec. II-D reconstruction, three planes X, Y, Z of [H][W].
 cudaError_t launch_xyz(const float *disp, int W, int H, double f_px, double baseline, double u0,
@@ -226,6 +249,7 @@ struct PairDesc {
     float *disp;
     int16_t *wta;                 // nullable
     float *rw, *mu_l, *inv_l, *mu_r, *inv_r, *dsub;
+    float2 *rowsh;                // [H] split row shifts
     void *vol_l, *vol_r;
     int16_t *lbl_l, *lbl_r;
 };

@@ -134,7 +134,8 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     const size_t b_ext = align256(H * WE * sizeof(float));
     const size_t b_vol = align256(H * WE * D * sr::vol_elem_bytes(p.vol_dtype));   // extended
     const size_t b_lbl = align256(npx * sizeof(int16_t));
-    const size_t need = 2 * b_img + 4 * b_ext + b_vol + 2 * b_lbl;
+    const size_t b_row = align256(H * sizeof(float2));
+    const size_t need = 2 * b_img + 4 * b_ext + b_vol + 2 * b_lbl + b_row;
     if (need > kSrNoallocScratchBytes) return SR_ERR_UNSUPPORTED;   // frame too large
 
     Addrs addrs;
@@ -150,6 +151,7 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     void *volx = take(b_vol);
     int16_t *lbl_l = reinterpret_cast<int16_t *>(take(b_lbl));
     int16_t *lbl_r = reinterpret_cast<int16_t *>(take(b_lbl));
+    float2 *rowsh = reinterpret_cast<float2 *>(take(b_row));
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     sr::AggDebug dbg;   // default bounded waits, reporting to the sticky timeout word
@@ -160,7 +162,7 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     if (!sr::encode_shear_map(&tmap, volx, p.vol_dtype, Wi, Hi, Di, p.agg_radius))
         return SR_ERR_CUDA;
     if (sr::launch_prep(d_left, d_right, pitch_bytes, Wi, Hi, Di, p.ncc_radius, alpha0, alpha1,
-                        delta, rw, mu_l, inv_l, mu_r, inv_r, st) != cudaSuccess ||
+                        delta, 0, rw, mu_l, inv_l, mu_r, inv_r, rowsh, st) != cudaSuccess ||
         sr::launch_ncc(false, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
                        p.ncc_radius, volx, p.vol_dtype, st, nullptr, WEi) != cudaSuccess ||
         sr::launch_agg_shear(&tmap, p.vol_dtype, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d,
@@ -172,9 +174,7 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
     post.post.lbl_r = lbl_r;
     post.post.disp = d_disp;
     post.post.wta = d_wta_or_null;
-    post.post.alpha0 = alpha0;
-    post.post.alpha1 = alpha1;
-    post.post.delta = delta;
+    post.post.rowsh = rowsh;
     post.post.lr_thresh = p.lr_thresh;
     if (sr::launch_agg(volx, p.vol_dtype, d_left, pitch_bytes, nullptr, Wi, Hi, Di, p.agg_radius,
                        p.gamma_d, p.gamma_r, lbl_l, dsub, nullptr, dbg, st, post, WEi) != cudaSuccess)

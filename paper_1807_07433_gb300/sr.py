@@ -27,7 +27,7 @@ SR_DEBUG_NO_BAND = 4
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
-           "sr_match_restricted",
+           "sr_match_restricted", "sr_match_rows",
            "sr_match_host", "sr_match_host_async", "sr_match_noalloc", "sr_noalloc_status",
            "sr_match_batch", "sr_set_autotune",
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
@@ -86,6 +86,7 @@ def load(path: str | None = None):
                 "sr_match_host": (i, [vp, vp, vp, vp]),
                 "sr_match_host_async": (i, [vp, vp, vp, vp]),
                 "sr_match_restricted": (i, [vp, vp, vp, i, vp, i, vp, vp]),
+                "sr_match_rows": (i, [vp, vp, vp, i, i, i, vp, vp]),
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
                 "sr_noalloc_status": (i, [vp]),
@@ -185,6 +186,13 @@ def sr_match_restricted(ctx, d_left, d_right, pitch_bytes: int, d_centre, radius
     _check(ctx, load().sr_match_restricted(ctx, _ptr(d_left), _ptr(d_right), int(pitch_bytes),
                                            _ptr(d_centre), int(radius), _ptr(d_disp),
                                            _ptr(d_wta_or_null)), "sr_match_restricted")
+
+
+def sr_match_rows(ctx, d_left_rows, d_right_rows, pitch_bytes: int, y0: int, y1: int,
+                  d_disp_rows, d_wta_rows_or_null=None) -> None:
+    _check(ctx, load().sr_match_rows(ctx, _ptr(d_left_rows), _ptr(d_right_rows),
+                                     int(pitch_bytes), int(y0), int(y1), _ptr(d_disp_rows),
+                                     _ptr(d_wta_rows_or_null)), "sr_match_rows")
 
 
 def sr_match_host(ctx, h_left, h_right, h_disp) -> None:
@@ -395,6 +403,19 @@ class Matcher:
             assert centre.dtype == torch.int16 and centre.is_contiguous()
         sr_match_restricted(self.ctx, left, right, pitch, centre, radius, disp, wta)
         return disp
+
+    def match_rows(self, left_rows, right_rows, y0, y1, disp_rows=None, wta_rows=None):
+        """sr_match_rows: rows [y0, y1) of the frame's disparity map from the
+        image rows r0..r1-1 (band plus halo; see bands.plan) given as
+        [r1 - r0, W] CUDA tensors."""
+        import torch
+        if disp_rows is None:
+            disp_rows = torch.empty((y1 - y0, self.W), dtype=torch.float32,
+                                    device=left_rows.device)
+        pitch = left_rows.stride(0) * left_rows.element_size()
+        assert right_rows.stride(0) == left_rows.stride(0), "left and right must share a pitch"
+        sr_match_rows(self.ctx, left_rows, right_rows, pitch, y0, y1, disp_rows, wta_rows)
+        return disp_rows
 
     def reconstruct(self, disp, xyz=None):
         import torch
