@@ -20,14 +20,15 @@
 //     128-bit load gives one tap's weight for four adjacent pixels.  Each
 //     weight is computed exactly once, and shared memory stays ~36 KB per
 //     CTA, so four CTAs (16 warps) fit on an SM;
-//   * lane = pair of disparities (float2), D/2 lanes share one 8 x 4 pixel
-//     block, so the weights a lane needs are the same for all those lanes
-//     (shared-memory broadcast);
-//   * each thread accumulates 8 x 4 pixels x 2 disparities = 64 sums.  For
-//     every streamed source row it loads the (8+2R) cost pairs of the row
-//     into registers once and reuses each for up to (2R+1) pixels x up to
-//     4 output rows; taps are the outer loop and pixels the inner one, so
-//     each tap issues 16 independent FMAs (no dependent FMA chains);
+//   * lane = 8 disparities of a block of 2 x 4 pixels; the D/8 lanes of a
+//     pixel group read the same weights (a broadcast) and each a different
+//     part of a cost column (two 16-byte loads, conflict-free);
+//   * each thread accumulates 2 x 4 pixels x 8 disparities = 64 sums, held as
+//     32 pairs of disparities that one paired multiply-add (fma.rn.f32x2)
+//     updates per tap, the weight paired with itself.  Tap columns are the
+//     outer loop: per tap column one new cost column enters the thread's
+//     sliding window and serves both pixels and every output row that uses
+//     the source row (32 independent paired multiply-adds);
 //   * epilogue: the sums are transposed through shared memory (over the
 //     rings) so that each lane scans the D costs of one pixel: argmax (ties
 //     to the smallest d), then Eq. 12 on the neighbours of the winner.  The
@@ -43,21 +44,68 @@
 
 namespace sr {
 
-constexpr int kAggTX = 32, kAggTY = 4, kAggPX = 8, kAggPix = kAggTX * kAggTY;
+constexpr int kAggTX = 32, kAggTY = 4, kAggPix = kAggTX * kAggTY;
+
+// Disparity of value k (0..7) held by lane sl of a pixel group in the layout
+// with 8 disparities per lane: for FP32 costs, k < 4 from the first half of
+// the disparities and k >= 4 from the second (two 16-byte loads that together
+// cover a cost column without bank conflicts); for 16-bit costs, 8
+// consecutive disparities (one 16-byte load).
+template <int D, typename VT>
+__device__ __forceinline__ int lane_disp8(int sl, int k) {
+    if (sizeof(VT) == 4) return (k >> 2) * (D / 2) + 4 * sl + (k & 3);
+    return 8 * sl + k;
+}
+// The 8 costs of lane sl in the cost column at col (layout [col][D]).
+__device__ __forceinline__ void load_col8(const float *col, int sl, int D, float *c) {
+    const float4 a = *reinterpret_cast<const float4 *>(col + 4 * sl);
+    const float4 b = *reinterpret_cast<const float4 *>(col + D / 2 + 4 * sl);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+template <typename H2>
+__device__ __forceinline__ void widen8(const uint4 &q, float *c) {
+    const H2 *h = reinterpret_cast<const H2 *>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float2 f;
+        if constexpr (std::is_same<H2, __half2>::value) f = __half22float2(h[i]);
+        else f = __bfloat1622float2(h[i]);
+        c[2 * i] = f.x;
+        c[2 * i + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void load_col8(const __half *col, int sl, int, float *c) {
+    widen8<__half2>(*reinterpret_cast<const uint4 *>(col + 8 * sl), c);
+}
+__device__ __forceinline__ void load_col8(const __nv_bfloat16 *col, int sl, int, float *c) {
+    widen8<__nv_bfloat162>(*reinterpret_cast<const uint4 *>(col + 8 * sl), c);
+}
 
 // SH: the tile reads a cost row sheared, pixel u at disparity d from column
 // u + d of an extended reference volume (the target view of Sec. II-B-1):
 // the ring slot holds D/CW boxes of CW disparities x BH pixels of a 2-D
 // tensor map, one box per CW-disparity chunk.  CW = 32 (128-byte box rows:
-// half the copies of CW = 16, and a lane's chunk words fall in distinct
-// banks) where MINB CTAs still fit an SM, else 16; with CW = 16, odd chunks
-// start one pixel earlier, which moves their words to the other half of the
-// banks (the chunk stride is a multiple of 32 words).
+// half the copies of CW = 16) where MINB CTAs still fit an SM, else 16; with
+// CW = 16, odd chunks start one pixel earlier, which moves their words to
+// the other half of the banks (the chunk stride is a multiple of 32 words).
 template <int R, int D, typename VT, bool SH = false>
 struct AggCfg {
-    static constexpr int SLOTS = D / 2;            // lanes per pixel group
+    // Lane layout.  A lane holds PX = 2 pixels x 4 output rows x DL = 8
+    // disparities: 64 sums, as 32 pairs of disparities, each updated by one
+    // paired multiply-add (fma.rn.f32x2) per tap.  Shared memory, not the FMA
+    // pipe, sets the pace of this loop, so the layout minimises shared-memory
+    // traffic per multiply-add for 64 sums: a weight pair (8 bytes) feeds 16
+    // multiply-adds and a cost column (8 disparities, 32 bytes) 2 pixels x 4
+    // rows.  Contiguous rows read a cost column with two 16-byte loads; the
+    // sheared rows of the target view read the 8 disparities of a pixel from
+    // the diagonal of their chunks, one element each.
+    static constexpr int DL = 8;
+    static constexpr int SLOTS = D / DL;           // lanes per pixel group
     static constexpr int G = 32 / SLOTS;           // pixel groups per warp
-    static constexpr int NW = 4 / G;               // warps per CTA
+    static constexpr int PX = 16 / DL;             // pixel columns of a group
+    static constexpr int PPG = kAggTY * PX;        // pixels of a group
+    static constexpr int NW = D / 16;              // warps per CTA
     static constexpr int NT = 32 * NW;
     static constexpr int MINB = 512 / NT;          // CTAs per SM to fit
     static constexpr int WS = 2 * R + 1;           // window side
@@ -349,15 +397,35 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
     __syncthreads();
 
     // ---- main loop: stream the tile's source rows --------------------------
+    constexpr int PX = C::PX, DL = C::DL;
     const int sl = lane % C::SLOTS, grp = lane / C::SLOTS;
-    const int bcol = warp * C::G + grp;          // 8-pixel block column, 0..3
-    const int bx = bcol * kAggPX;                // first tile column of the block
+    const int bcol = warp * C::G + grp;          // block column of PX pixels
+    const int bx = bcol * PX;                    // first tile column of the block
+    // sheared rows with 8 disparities per lane: pair q of the lane holds
+    // disparities m_q and m_q + D/2, m_q = (sl + SLOTS q + 8 grp) mod D/2, so
+    // that the 32 lanes of a warp read 32 different banks for D = 64; the
+    // element of disparity d for tile pixel i sits at offset
+    // (d / CW) CSE + (i + d % CW + SHIFT ((d / CW) & 1)) CW + d % CW
+    int sh_m[4] = {0, 0, 0, 0}, sh_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if constexpr (SH) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            sh_m[q] = (sl + C::SLOTS * q + 8 * grp) % (D / 2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int d = sh_m[q] + h * (D / 2), c = d / C::CW, m = d % C::CW;
+                sh_off[q + 4 * h] = c * C::CSE + (m + C::SHIFT * (c & 1)) * C::CW + m;
+            }
+        }
+    }
 
-    float2 acc[kAggTY][kAggPX];
+    float2 acc[kAggTY][PX][DL / 2];
 #pragma unroll
     for (int py = 0; py < kAggTY; ++py)
 #pragma unroll
-        for (int px = 0; px < kAggPX; ++px) acc[py][px] = make_float2(0.0f, 0.0f);
+        for (int px = 0; px < PX; ++px)
+#pragma unroll
+            for (int q = 0; q < DL / 2; ++q) acc[py][px][q] = make_float2(0.0f, 0.0f);
 
 #pragma unroll 1
     for (int j = 0; j < C::TYE; ++j) {
@@ -377,42 +445,53 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
         if (y >= 0 && y < H) {
             mbar_wait(bars + (j & 1), (ph >> (j & 1)) & 1u, wait_cycles, err);
             const float *ws = wring + (j % C::WSL) * C::WRING + bx;
-            float2 cst[kAggPX + 2 * R];
-            if (SH) {   // lane sl: disparities sl and sl + SLOTS (see the epilogue)
-                constexpr int CW = C::CW;
-                const VT *slot = ring + (j & 1) * C::RINGS + bx * CW;
-                const int da = sl, db = sl + C::SLOTS;
-                const VT *ra = slot + (da / CW) * C::CSE +
-                               ((da % CW) + C::SHIFT * ((da / CW) & 1)) * CW + (da % CW);
-                const VT *rb = slot + (db / CW) * C::CSE +
-                               ((db % CW) + C::SHIFT * ((db / CW) & 1)) * CW + (db % CW);
+            // taps outer: a cost column (8 disparities) enters per tap
+            // column and serves PX pixels x the valid output rows
+            const VT *rs = SH ? ring + (j & 1) * C::RINGS + bx * C::CW
+                              : ring + (j & 1) * C::RINGS + bx * D;
+            auto body = [&](auto all_rows) {
+                float2 cst[PX + 2 * R][4];
+                auto load_col = [&](int i) {
+                    if constexpr (SH) {
+                        // pair q: disparities sh_m[q] and sh_m[q] + D/2, on
+                        // the diagonal of their chunks (offsets sh_off)
 #pragma unroll
-                for (int i = 0; i < kAggPX + 2 * R; ++i)
-                    cst[i] = make_float2(load_one(ra + i * CW), load_one(rb + i * CW));
-            } else {
-                const VT *rs = ring + (j & 1) * C::RINGS + bx * D + 2 * sl;
+                        for (int q = 0; q < 4; ++q)
+                            cst[i][q] = make_float2(load_one(rs + sh_off[q] + i * C::CW),
+                                                    load_one(rs + sh_off[q + 4] + i * C::CW));
+                    } else {
+                        float c[8];
+                        load_col8(rs + i * D, sl, D, c);
 #pragma unroll
-                for (int i = 0; i < kAggPX + 2 * R; ++i)
-                    cst[i] = load_pair(rs + i * D);
-            }
+                        for (int q = 0; q < 4; ++q) cst[i][q] = make_float2(c[2 * q], c[2 * q + 1]);
+                    }
+                };
 #pragma unroll
-            for (int py = 0; py < kAggTY; ++py) {
-                const int dyi = j - py;
-                if (dyi >= 0 && dyi < C::WS) {
-                    const float *wb = ws + (py * C::WS) * kAggTX;
+                for (int i = 0; i < PX - 1; ++i) load_col(i);
 #pragma unroll
-                    for (int dx = 0; dx < C::WS; ++dx) {
-                        const float4 wa = *reinterpret_cast<const float4 *>(wb + dx * kAggTX);
-                        const float4 wc = *reinterpret_cast<const float4 *>(wb + dx * kAggTX + 4);
-                        const float w[kAggPX] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+                for (int dx = 0; dx < C::WS; ++dx) {
+                    load_col(dx + PX - 1);
 #pragma unroll
-                        for (int px = 0; px < kAggPX; ++px) {
-                            acc[py][px].x = fmaf(w[px], cst[px + dx].x, acc[py][px].x);
-                            acc[py][px].y = fmaf(w[px], cst[px + dx].y, acc[py][px].y);
+                    for (int py = 0; py < kAggTY; ++py) {
+                        if (decltype(all_rows)::value || (unsigned)(j - py) < (unsigned)C::WS) {
+                            // the weights of the lane's two pixels, each
+                            // paired with itself for the paired multiply-add
+                            const float2 w2 = *reinterpret_cast<const float2 *>(
+                                ws + (py * C::WS + dx) * kAggTX);
+                            const float2 w[PX] = {make_float2(w2.x, w2.x), make_float2(w2.y, w2.y)};
+#pragma unroll
+                            for (int px = 0; px < PX; ++px)
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    acc[py][px][q] = __ffma2_rn(w[px], cst[px + dx][q], acc[py][px][q]);
                         }
                     }
                 }
-            }
+            };
+            if (j >= kAggTY - 1 && j < C::WS)
+                body(std::integral_constant<bool, true>());   // all output rows use row j
+            else
+                body(std::integral_constant<bool, false>());
         }
         ph ^= 1u << (j & 1);   // every source row completes one phase of its slot
         __syncthreads();
@@ -435,19 +514,30 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
             wsum[py * kAggTX + px] = s > 0.0f ? s : 1.0f;
         }
     }
-    float *E = smem + warp * (32 * C::G) * (D + 1);     // this warp's pixels x D
+    float *E = smem + warp * (C::PPG * C::G) * (D + 1);     // this warp's pixels x D
 #pragma unroll
     for (int py = 0; py < kAggTY; ++py)
 #pragma unroll
-        for (int px = 0; px < kAggPX; ++px) {
-            float *e = E + (grp * 32 + py * kAggPX + px) * (D + 1);
-            e[SH ? sl : 2 * sl] = acc[py][px].x;
-            e[SH ? sl + C::SLOTS : 2 * sl + 1] = acc[py][px].y;
+        for (int px = 0; px < PX; ++px) {
+            float *e = E + (grp * C::PPG + py * PX + px) * (D + 1);
+            if constexpr (SH) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    e[sh_m[q]] = acc[py][px][q].x;
+                    e[sh_m[q] + D / 2] = acc[py][px][q].y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    e[lane_disp8<D, VT>(sl, 2 * q)] = acc[py][px][q].x;
+                    e[lane_disp8<D, VT>(sl, 2 * q + 1)] = acc[py][px][q].y;
+                }
+            }
         }
     __syncthreads();
-    for (int pw = lane; pw < 32 * C::G; pw += 32) {
-        const int g = pw >> 5, py = (pw & 31) / kAggPX, px = pw % kAggPX;
-        const int tpx = (warp * C::G + g) * kAggPX + px;
+    for (int pw = lane; pw < C::PPG * C::G; pw += 32) {
+        const int g = pw / C::PPG, py = (pw % C::PPG) / PX, px = pw % PX;
+        const int tpx = (warp * C::G + g) * PX + px;
         const int u = x0 + tpx, v = y0 + py;
         if (u >= W || v >= H) continue;
         const float *e = E + pw * (D + 1);
@@ -496,9 +586,9 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
         }
     }
     if (agg) {
-        for (int pw = 0; pw < 32 * C::G; ++pw) {
-            const int g = pw >> 5, py = (pw & 31) / kAggPX, px = pw % kAggPX;
-            const int tpx = (warp * C::G + g) * kAggPX + px;
+        for (int pw = 0; pw < C::PPG * C::G; ++pw) {
+            const int g = pw / C::PPG, py = (pw % C::PPG) / PX, px = pw % PX;
+            const int tpx = (warp * C::G + g) * PX + px;
             const int u = x0 + tpx, v = y0 + py;
             if (u >= W || v >= H) continue;
             const float sc = 1.0f / wsum[py * kAggTX + tpx];
