@@ -134,6 +134,116 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlSampler:
+    """Samples SM clock, its maximum, power and clock-event (throttle)
+    reasons through NVML (libnvidia-ml, loaded with ctypes) every ~2 ms on a
+    background thread while running, so that even a timed region of a few
+    tens of milliseconds gets several samples.  Falls back to ClockSampler
+    (nvidia-smi every 200 ms) when NVML cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device_index: int, period_s: float = 0.002):
+        self.idx = device_index
+        self.period = period_s
+        self.samples: list[tuple[float, float, int, float]] = []
+        self.h = None
+        self.lib = None
+        self.stop = threading.Event()
+        self.t = None
+        self.fallback = None
+
+    def _open(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        ok = False
+        try:   # the same GPU as the CUDA device: match the PCI bus id, else the UUID
+            import torch
+            props = torch.cuda.get_device_properties(self.idx)
+            bus = getattr(props, "pci_bus_id", None)
+            dom = getattr(props, "pci_domain_id", 0)
+            dv = getattr(props, "pci_device_id", 0)
+            if bus is not None:
+                busid = f"{dom:08x}:{bus:02x}:{dv:02x}.0".encode()
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(busid, ctypes.byref(h)) == 0
+            if not ok and getattr(props, "uuid", None) is not None:
+                uu = f"GPU-{props.uuid}".encode()
+                ok = lib.nvmlDeviceGetHandleByUUID(uu, ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            order = [x for x in vis.split(",") if x.strip().isdigit()]
+            nidx = int(order[self.idx]) if self.idx < len(order) else self.idx
+            if lib.nvmlDeviceGetHandleByIndex_v2(nidx, ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        self.lib, self.h = lib, h
+
+    def _read(self):
+        import ctypes
+        clk, mx, pw = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint()
+        reasons = ctypes.c_ulonglong()
+        get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0 and \
+                    self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                r = get_reasons(self.h, ctypes.byref(reasons))
+                p = self.lib.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(pw))
+                self.samples.append((float(clk.value), float(mx.value),
+                                     int(reasons.value) if r == 0 else 0,
+                                     pw.value / 1000.0 if p == 0 else float("nan")))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        try:
+            self._open()
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.01)
+        except Exception:
+            self.fallback = ClockSampler(self.idx).__enter__()
+        return self
+
+    def __exit__(self, *exc):
+        if self.fallback is not None:
+            self.fallback.__exit__(*exc)
+            return
+        self.stop.set()
+        if self.t is not None:
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if self.fallback is not None:
+            out = self.fallback.summary()
+            if out is not None:
+                out["source"] = "nvidia-smi every 200 ms"
+            return out
+        if not self.samples:
+            return None
+        sm = [x[0] for x in self.samples]
+        reasons = set()
+        for _, _, mask, _ in self.samples:
+            for bit, name in self.REASONS.items():
+                if mask & bit:
+                    reasons.add(name)
+        pw = [x[3] for x in self.samples if x[3] == x[3]]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+                "sm_mhz_min": min(sm), "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": round(max(pw), 1) if pw else None,
+                "source": "NVML every ~2 ms"}
+
+
+def step_stats(ms: list[float]) -> dict:
+    """Median, mean and 10th / 90th percentiles of per-step times (ms)."""
+    q = statistics.quantiles(ms, n=10, method="inclusive") if len(ms) >= 2 else [ms[0]] * 9
+    return {"median": round(statistics.median(ms), 5), "mean": round(sum(ms) / len(ms), 5),
+            "p10": round(q[0], 5), "p90": round(q[8], 5), "n": len(ms)}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -188,26 +298,29 @@ def run_ours(args, w):
         m.match(dl, dr, disp)
     torch.cuda.synchronize()
 
+    # Timed region: K matches, each bracketed by CUDA events on the context's
+    # stream; the L2 flush runs between them, outside the events.  The
+    # library records each match's stage events into a ring (no
+    # synchronisation between steps); they are read after the region.
     sr.sr_set_profiling(m.ctx, True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_rows = []
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
+    with NvmlSampler(local) as clk:
         for k in range(args.steps):
             flush.zero_()                       # L2 flush outside the timed events
             starts[k].record(stream)
             m.match(dl, dr, disp)
             ends[k].record(stream)
-            stage_rows.append(sr.sr_stage_times(m.ctx))   # synchronises the stream
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    stage_rows = sr.sr_stage_times_history(m.ctx, args.steps)
     total_ms_max = max_over_ranks(sum(step_ms), ws, dev)
     sr.sr_set_profiling(m.ctx, False)
 
@@ -258,7 +371,8 @@ def run_ours(args, w):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "fps": round(fps, 2),
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": round(ms_step, 5), "step_ms": step_stats(step_ms),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: seeded textured road plane with potholes and grooves (generator "
                 "paper_1807_07433_gb300/synth.py, seed 2); stands in for the paper's ZED road data",
@@ -288,13 +402,162 @@ def run_ours(args, w):
     return line
 
 
-def oracle_sample(w, target_s: float, rows_hint: int | None = None):
+def _timed_steps(fn, steps: int, warmup: int, stream, flush):
+    """Per-step device times (ms) of fn: CUDA events on stream around each
+    call, L2 flushed before each (outside the events), no synchronisation
+    between steps."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+
+def _faster_beyond_spread(form: dict, base: dict) -> bool:
+    """The form's 90th-percentile step time lies below the base form's 10th."""
+    return form["step_ms"]["p90"] < base["step_ms"]["p10"]
+
+
+def forms_720p(w, steps: int, warmup: int, dev) -> dict:
+    """The 1280x720x64 workload in each volume type (FP32, FP16, BF16 storage,
+    FP32 arithmetic), steps steps each, and the FP32 step followed by
+    sr_reconstruct (Sec. II-D)."""
+    import torch
+    from paper_1807_07433_gb300 import sr, synth
+    W, H, D = w.scene.W, w.scene.H, w.D
+    left, right, _ = synth.make_pair(w.scene)
+    stream = torch.cuda.current_stream(dev)
+    dl, dr = torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)
+    disp = torch.empty((H, W), dtype=torch.float32, device=dev)
+    xyz = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, vt in (("fp32", sr.SR_VOL_F32), ("fp16", sr.SR_VOL_F16), ("bf16", sr.SR_VOL_BF16)):
+        with sr.Matcher(W, H, D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                        vol_dtype=vt, stream=stream) as m:
+            m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+            m.set_camera(w.f_px, w.baseline_mm)
+            ms = _timed_steps(lambda: m.match(dl, dr, disp), steps, warmup, stream, flush)
+            st = step_stats(ms)
+            out[name] = {"mdes": round(mdes(W, H, D, st["median"] * 1e-3), 1),
+                         "fps": round(1e3 / st["median"], 1), "step_ms": st}
+            if name == "fp32":
+                ms = _timed_steps(lambda: (m.match(dl, dr, disp), m.reconstruct(disp, xyz)),
+                                  steps, warmup, stream, flush)
+                out["fp32_with_reconstruct"] = {"step_ms": step_stats(ms)}
+    for name in ("fp16", "bf16"):
+        out[name]["vs_fp32_median"] = round(out["fp32"]["step_ms"]["median"] /
+                                            out[name]["step_ms"]["median"], 4)
+        out[name]["faster_beyond_spread"] = _faster_beyond_spread(out[name], out["fp32"])
+    return out
+
+
+def _gen_pairs_spawn(scenes):
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_pair, scenes)
+
+
+def forms_batch(steps: int, warmup: int, dev, data=None) -> dict:
+    """The 64-pair workload (16 each of 672x376, 1280x720, 1920x1080,
+    2208x1242, D = 64, NCC 7x7, bilateral 11x11): 64 sequential plain FP32
+    sr_match calls, and sr_match_batch (autotuned schedule in a CUDA graph)
+    with FP32 and FP16 volumes; per-step times of the whole batch."""
+    import torch
+    from paper_1807_07433_gb300 import sr, synth
+    ws = synth.batch_workloads()
+    if data is None:
+        data = _gen_pairs_spawn([w.scene for w in ws])
+    D = ws[0].D
+    stream = torch.cuda.current_stream(dev)
+    ins, outs = [], []
+    for left, right in data:
+        H, W = left.shape
+        ins.append((torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)))
+        outs.append(torch.empty((H, W), dtype=torch.float32, device=dev))
+    total_de = sum(w.scene.W * w.scene.H * D for w in ws)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+    ctxs = {}
+    for w in ws:
+        key = (w.scene.W, w.scene.H)
+        if key not in ctxs:
+            ctxs[key] = sr.Matcher(w.scene.W, w.scene.H, D, w.ncc_r, w.agg_r, w.gamma_d,
+                                   w.gamma_r, w.lr_thresh, stream=stream)
+
+    def seq():
+        for w, (dl, dr), out in zip(ws, ins, outs):
+            m = ctxs[(w.scene.W, w.scene.H)]
+            m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+            m.match(dl, dr, out)
+    st = step_stats(_timed_steps(seq, steps, warmup, stream, flush))
+    res["sequential_fp32"] = {"mdes": round(total_de / (st["median"] * 1e-3) * 1e-6, 1),
+                              "step_ms": st}
+    for m in ctxs.values():
+        m.close()
+    w0 = ws[0]
+    for name, vt in (("batched_fp32", sr.SR_VOL_F32), ("batched_fp16", sr.SR_VOL_F16)):
+        with sr.Matcher(8, 8, D, w0.ncc_r, w0.agg_r, w0.gamma_d, w0.gamma_r, w0.lr_thresh,
+                        vol_dtype=vt, stream=stream) as m:
+            sr.sr_set_autotune(m.ctx, True)
+            descs = [sr.make_pair_desc(dl, dr, out, w.scene.alpha0, w.scene.alpha1, w.delta)
+                     for w, (dl, dr), out in zip(ws, ins, outs)]
+            sr.sr_match_batch(m.ctx, descs)        # tunes on first use
+            torch.cuda.synchronize()
+            st = step_stats(_timed_steps(lambda: sr.sr_match_batch(m.ctx, descs), steps,
+                                         warmup, stream, flush))
+            res[name] = {"mdes": round(total_de / (st["median"] * 1e-3) * 1e-6, 1),
+                         "step_ms": st, "schedule": sr.sr_batch_info(m.ctx)}
+        torch.cuda.empty_cache()
+    for name in ("batched_fp32", "batched_fp16"):
+        res[name]["vs_sequential_fp32_median"] = round(
+            res["sequential_fp32"]["step_ms"]["median"] / res[name]["step_ms"]["median"], 4)
+        res[name]["faster_beyond_spread"] = _faster_beyond_spread(res[name],
+                                                                  res["sequential_fp32"])
+    return {"pairs": len(ws), "total_disparity_evaluations": total_de, "forms": res}
+
+
+def cpu_baseline_protocol(w2, target_s: float = 8.0) -> dict:
+    """The FP64 oracle on the host cores: the 1280x720x64 frame on a band of
+    rows with all cores and with one core, the 160x120x16 frame whole, and a
+    band of the 1920x1080x64 frame, each sized to about target_s seconds."""
+    import oracle
+    from paper_1807_07433_gb300 import synth
+    cores = os.cpu_count() or 1
+    out = {}
+    val, dt, rows, n = oracle_sample(w2, target_s=target_s)
+    out["c2_all_cores"] = {"value": round(val, 4), "cores": n, "seconds": round(dt, 2),
+                           "rows": list(rows)}
+    oracle.set_num_threads(1)
+    val1, dt1, rows1, _ = oracle_sample(w2, target_s=target_s, threads=1)
+    out["c2_one_core"] = {"value": round(val1, 4), "cores": 1, "seconds": round(dt1, 2),
+                          "rows": list(rows1)}
+    oracle.set_num_threads(cores)
+    val, dt, rows, n = oracle_sample(synth.C1, target_s=min(target_s, 2.0))
+    out["c1_all_cores"] = {"value": round(val, 4), "cores": n, "seconds": round(dt, 2),
+                           "rows": list(rows)}
+    val, dt, rows, n = oracle_sample(synth.C3, target_s=target_s)
+    out["c3_all_cores"] = {"value": round(val, 4), "cores": n, "seconds": round(dt, 2),
+                           "rows": list(rows)}
+    return out
+
+
+def oracle_sample(w, target_s: float, rows_hint: int | None = None, threads: int | None = None):
     """Time the FP64 oracle on a band of output rows sized for about
-    target_s seconds; returns (Mde/s, seconds, rows, cores)."""
+    target_s seconds, on threads host cores (default: all); returns (Mde/s,
+    seconds, rows, cores)."""
     import oracle
     from paper_1807_07433_gb300 import synth
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     oracle.set_num_threads(cores)
     left, right, _ = synth.make_pair(w.scene)
     p = oracle.Params(W=w.scene.W, H=w.scene.H, D=w.D, ncc_r=w.ncc_r, agg_r=w.agg_r,
@@ -847,6 +1110,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP16/BF16 and batched forms of the default line")
+    ap.add_argument("--form-steps", type=int, default=200,
+                    help="timed steps of each extra form (default 200)")
     ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit", "accuracy",
                                                 "restricted"), default=None,
                     help="print a report instead of the benchmark line")
@@ -887,16 +1154,33 @@ def main():
     if not os.path.exists(sr.LIB_PATH):
         import __graft_entry__
         __graft_entry__.build()
+    ws_env, _, _ = _dist()
+    batch_data = None
+    if ws_env == 1 and not args.no_forms:
+        # the 64 pairs of the batched form, rendered before any CUDA call
+        batch_data = _gen_pairs_spawn([x.scene for x in synth.batch_workloads()])
     line = run_ours(args, w)
     if line is None:
         return
     ws = line["n_gpus"]
+    if ws == 1 and not args.no_forms:
+        import torch
+        dev = torch.device("cuda", 0)
+        with NvmlSampler(0) as clk:
+            line["forms_720p"] = forms_720p(w, args.form_steps, 10, dev)
+            line["forms_batch"] = forms_batch(args.form_steps, 3, dev, batch_data)
+        line["forms_clocks"] = clk.summary()
+        line["forms_note"] = (f"{args.form_steps} timed steps per form (median, mean, p10, p90 "
+                              "of per-step CUDA-event times, L2 flushed between steps); "
+                              "faster_beyond_spread: the form's p90 below the base form's p10")
     if ws == 1 and not args.no_cpu_baseline:
-        val, dt, rows, cores = oracle_sample(w, target_s=10.0)
+        proto = cpu_baseline_protocol(w)
+        c2 = proto["c2_all_cores"]
         line["cpu_baseline"] = {
-            "value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"output rows {rows[0]}..{rows[1] - 1} of the same frame, repeated for "
-                      f"{dt:.1f} s, FP64 oracle with OpenMP"}
+            "value": c2["value"], "unit": UNIT, "cores": c2["cores"], "kind": "oracle",
+            "sample": f"output rows {c2['rows'][0]}..{c2['rows'][1] - 1} of the same frame, "
+                      f"repeated for {c2['seconds']:.1f} s, FP64 oracle with OpenMP",
+            "protocol": proto}
     print(json.dumps(line), flush=True)
 
 

@@ -406,12 +406,19 @@ sr_status sr_set_debug(sr_ctx *ctx, int flags);
 sr_status sr_synchronize(sr_ctx *ctx);
 
 /* Per-stage timing.  While enabled, sr_match records a CUDA event before
- * and after each stage on the context's stream.  sr_stage_times
- * synchronises the stream and writes, for the most recent sr_match, the
- * duration in milliseconds of each stage into ms[0..n) in the order of
- * sr_stage_names(); it returns the number of stages in *count. */
+ * and after each stage on the context's stream, in a ring that keeps the
+ * events of the last 512 matches (created on the first enable; enabling
+ * restarts the count).  Recording does not synchronise anything.
+ * sr_stage_times synchronises the stream and writes, for the most recent
+ * sr_match, the duration in milliseconds of each stage into ms[0..n) in the
+ * order of sr_stage_names(); it returns the number of stages in *count.
+ * sr_stage_times_history writes the stage durations of the most recent
+ * min(max_matches, matches recorded, 512) matches, oldest first, stage s of
+ * match k at ms[k * stages + s]; *count receives the number of matches.
+ * Both return SR_ERR_STATE when no match has been recorded. */
 sr_status sr_set_profiling(sr_ctx *ctx, int enable);
 sr_status sr_stage_times(sr_ctx *ctx, float *ms, int n, int *count);
+sr_status sr_stage_times_history(sr_ctx *ctx, float *ms, int max_matches, int *count);
 const char *sr_stage_names(void);   /* comma-separated stage names */
 
 /* Number of kernel launches one sr_match queues (for launch accounting). */

@@ -254,8 +254,11 @@ void free_all(sr_ctx *c) {
                     c->nrange};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    for (auto &e : c->ev)
-        if (e) cudaEventDestroy(e);
+    if (c->ev_ring) {
+        for (int i = 0; i < kProfRing * (kStages + 1); ++i)
+            if (c->ev_ring[i]) cudaEventDestroy(c->ev_ring[i]);
+        delete[] c->ev_ring;
+    }
     for (int i = 0; i < 2; ++i) {
         if (c->ev_up[i]) cudaEventDestroy(c->ev_up[i]);
         if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
@@ -424,7 +427,6 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
     if (e == cudaSuccess) e = dalloc(&c->lbl_r, npx);
     if (e == cudaSuccess) e = dalloc(&c->d_err, 1);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
-    for (int i = 0; i <= kStages && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();   // clear a sticky allocation error
         free_all(c);
@@ -477,18 +479,46 @@ sr_status sr_set_debug(sr_ctx *c, int flags) {
 
 sr_status sr_set_profiling(sr_ctx *c, int enable) {
     if (!c) return SR_ERR_INVALID_ARG;
+    if (enable && !c->ev_ring) {
+        c->ev_ring = new (std::nothrow) cudaEvent_t[kProfRing * (kStages + 1)]();
+        if (!c->ev_ring) return SR_ERR_OOM;
+        for (int i = 0; i < kProfRing * (kStages + 1); ++i)
+            SR_TRY(c, cudaEventCreate(&c->ev_ring[i]), "cudaEventCreate");
+    }
     c->profiling = enable != 0;
     c->timed = false;
+    c->prof_count = 0;
     return SR_OK;
 }
 
 sr_status sr_stage_times(sr_ctx *c, float *ms, int n, int *count) {
     if (!c || (n > 0 && !ms)) return SR_ERR_INVALID_ARG;
     if (count) *count = kStages;
-    if (!c->timed) return SR_ERR_STATE;
-    SR_TRY(c, cudaEventSynchronize(c->ev[kStages]), "cudaEventSynchronize");
+    if (!c->timed || c->prof_count < 1) return SR_ERR_STATE;
+    const cudaEvent_t *e = c->ev_ring + ((c->prof_count - 1) % kProfRing) * (kStages + 1);
+    SR_TRY(c, cudaEventSynchronize(e[kStages]), "cudaEventSynchronize");
     for (int i = 0; i < kStages && i < n; ++i)
-        SR_TRY(c, cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]), "cudaEventElapsedTime");
+        SR_TRY(c, cudaEventElapsedTime(&ms[i], e[i], e[i + 1]), "cudaEventElapsedTime");
+    return take_device_error(c);
+}
+
+sr_status sr_stage_times_history(sr_ctx *c, float *ms, int max_matches, int *count) {
+    if (!c || !ms || max_matches < 1 || !count) return SR_ERR_INVALID_ARG;
+    *count = 0;
+    if (!c->ev_ring || c->prof_count < 1) return SR_ERR_STATE;
+    long long m = c->prof_count < kProfRing ? c->prof_count : kProfRing;
+    if (m > max_matches) m = max_matches;
+    const long long first = c->prof_count - m;
+    SR_TRY(c, cudaEventSynchronize(c->ev_ring[((c->prof_count - 1) % kProfRing) * (kStages + 1) +
+                                              kStages]),
+           "cudaEventSynchronize");
+    for (long long k = 0; k < m; ++k) {
+        const cudaEvent_t *e = c->ev_ring + ((first + k) % kProfRing) * (kStages + 1);
+        for (int i = 0; i < kStages; ++i)
+            SR_TRY(c, cudaEventElapsedTime(&ms[k * kStages + i], e[i], e[i + 1]),
+                   "cudaEventElapsedTime");
+    }
+    *count = (int)m;
     return take_device_error(c);
 }
 
@@ -509,8 +539,9 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     const bool prof = c->profiling;
     const bool keep = (c->debug & SR_DEBUG_KEEP_AGG) != 0;
     int stage = 0;
+    cudaEvent_t *evs = prof ? c->ev_ring + (c->prof_count % kProfRing) * (kStages + 1) : nullptr;
     auto mark = [&]() -> cudaError_t {
-        return prof ? cudaEventRecord(c->ev[stage++], st) : cudaSuccess;
+        return prof ? cudaEventRecord(evs[stage++], st) : cudaSuccess;
     };
     c->matched = false;
     c->timed = false;
@@ -558,6 +589,7 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     c->vol_ext = true;
     c->agg_valid = keep;
     c->timed = prof;
+    if (prof) ++c->prof_count;
     return SR_OK;
 }
 

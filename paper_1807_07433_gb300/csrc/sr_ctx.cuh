@@ -8,6 +8,7 @@
 #include "sr_internal.cuh"
 
 constexpr int kStages = 4;    // stages of one sr_match with profiling events
+constexpr int kProfRing = 512;   // matches whose stage events are kept
 
 struct SrBatch;               // batched-form state, defined in sr_batch.cu
 void sr_batch_free(sr_ctx *c);
@@ -54,7 +55,11 @@ struct sr_ctx {
     int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
     bool matched = false, agg_valid = false;
     bool profiling = false, timed = false;
-    cudaEvent_t ev[kStages + 1] = {};
+    // stage events of the last kProfRing matches while profiling: match k
+    // uses ev_ring[(k % kProfRing) * (kStages + 1) ...]; prof_count matches
+    // recorded since profiling was enabled
+    cudaEvent_t *ev_ring = nullptr;
+    long long prof_count = 0;
     char err[256] = {0};
     SrBatch *batch = nullptr;        // batched-form resources (sr_batch.cu), on first use
     // sr_grad_plane scratch, on first use: wsum and grw [H*W], FP64 partials and,

@@ -33,7 +33,7 @@ EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
            "sr_fit_alpha", "sr_fit_roll",
            "sr_get_buffer", "sr_set_debug",
-           "sr_set_profiling", "sr_synchronize", "sr_stage_times", "sr_stage_names", "sr_kernels_per_match",
+           "sr_set_profiling", "sr_synchronize", "sr_stage_times", "sr_stage_times_history", "sr_stage_names", "sr_kernels_per_match",
            "sr_status_str", "sr_last_error", "sr_version")
 
 
@@ -105,6 +105,7 @@ def load(path: str | None = None):
                 "sr_set_profiling": (i, [vp, i]),
                 "sr_synchronize": (i, [vp]),
                 "sr_stage_times": (i, [vp, ctypes.POINTER(f), i, ctypes.POINTER(i)]),
+                "sr_stage_times_history": (i, [vp, ctypes.POINTER(f), i, ctypes.POINTER(i)]),
                 "sr_stage_names": (ctypes.c_char_p, []),
                 "sr_kernels_per_match": (i, [vp]),
                 "sr_status_str": (ctypes.c_char_p, [i]),
@@ -316,6 +317,18 @@ def sr_stage_times(ctx) -> dict:
     _check(ctx, load().sr_stage_times(ctx, arr, n, ctypes.byref(cnt)), "sr_stage_times")
     names = sr_stage_names()
     return {names[k]: float(arr[k]) for k in range(cnt.value)}
+
+
+def sr_stage_times_history(ctx, max_matches: int) -> list[dict]:
+    """Stage durations (ms) of the most recent matches recorded while
+    profiling, oldest first (at most 512)."""
+    names = sr_stage_names()
+    arr = (ctypes.c_float * (int(max_matches) * len(names)))()
+    cnt = ctypes.c_int()
+    _check(ctx, load().sr_stage_times_history(ctx, arr, int(max_matches), ctypes.byref(cnt)),
+           "sr_stage_times_history")
+    return [{names[s]: float(arr[k * len(names) + s]) for s in range(len(names))}
+            for k in range(cnt.value)]
 
 
 def sr_stage_names() -> list[str]:

@@ -243,6 +243,18 @@ def test_stage_timing_and_launch_count():
         assert list(t) == sr.sr_stage_names()
         assert all(v >= 0.0 for v in t.values())
         assert sr.sr_kernels_per_match(m.ctx) == 4
+        # the ring keeps every match's events; no synchronisation in between
+        dl, dr = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+        for _ in range(5):
+            m.match(dl, dr)
+        hist = sr.sr_stage_times_history(m.ctx, 100)
+        assert len(hist) == 6 and all(list(h) == sr.sr_stage_names() for h in hist)
+        assert all(v > 0.0 for h in hist for v in h.values())
+        assert sr.sr_stage_times_history(m.ctx, 2) == hist[-2:]
+        sr.sr_set_profiling(m.ctx, True)            # re-enabling restarts the count
+        with pytest.raises(sr.SrError) as e:
+            sr.sr_stage_times_history(m.ctx, 4)
+        assert e.value.status == sr.SR_ERR_STATE
 
 
 def test_error_paths_on_device():
