@@ -964,7 +964,7 @@ def accuracy_report(steps: int, warmup: int):
     import numpy as np
     import torch
 
-    from paper_1807_07433_gb300 import sr, synth
+    from paper_1807_07433_gb300 import accuracy, sr, synth
     w = synth.C2
     sc = w.scene
     left, right, d_true = synth.make_pair(sc)
@@ -979,48 +979,12 @@ def accuracy_report(steps: int, warmup: int):
         m.set_camera(f, B, u0, v0)
         disp = m.match(torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev))
         xyz = m.reconstruct(disp).cpu().numpy().astype(np.float64)
-    vv, uu = np.mgrid[0:H, 0:W].astype(np.float64)
-    Zt = f * B / d_true
-    xyz_t = np.stack([(uu - u0) * Zt / f, (vv - v0) * Zt / f, Zt])
-
-    groove_mask = np.zeros((H, W), bool)
-    for pts, half_w, _ in grooves:
-        for (x0, y0), (x1, y1) in zip(pts[:-1], pts[1:]):
-            ex, ey = x1 - x0, y1 - y0
-            t = np.clip(((uu - x0) * ex + (vv - y0) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
-            groove_mask |= np.hypot(uu - (x0 + t * ex), vv - (y0 + t * ey)) < half_w + 3.0
-
-    def plane_dist(P, Q):
-        """distances of points Q (N x 3) to the least-squares plane of P (M x 3)"""
-        c = P.mean(0)
-        n = np.linalg.svd(P - c, full_matrices=False)[2][-1]
-        return np.abs((Q - c) @ n)
-
-    rows = []
-    for k, (uk, vk, a, s) in enumerate(pots):
-        if not (6 * s <= uk < W - 6 * s and 6 * s <= vk < H - 6 * s):
-            continue
-        if any(j != k and np.hypot(uk - uj, vk - vj) < 6 * s + 4 * sj
-               for j, (uj, vj, _, sj) in enumerate(pots)):
-            continue
-        r = np.hypot(uu - uk, vv - vk)
-        ring = (r >= 4 * s) & (r <= 6 * s) & ~groove_mask
-        core = (r <= 0.5 * s) & ~groove_mask
-        if groove_mask[(r <= 6 * s)].any() or (d_true[core] <= sc.alpha0 + sc.alpha1 * vv[core] - 2.0).any():
-            continue
-        ok_ring = ring & np.isfinite(xyz[2])
-        ok_core = core & np.isfinite(xyz[2])
-        if ok_ring.sum() < 50 or ok_core.sum() < 5:
-            continue
-        meas = plane_dist(xyz[:, ok_ring].T, xyz[:, ok_core].T)
-        true = plane_dist(xyz_t[:, ok_ring].T, xyz_t[:, ok_core].T)
-        err = meas - true
-        rows.append({"pothole": k, "u": round(uk, 1), "v": round(vk, 1), "depth_px": round(a, 3),
-                     "sigma_px": round(s, 2), "true_depth_mm": round(float(true.mean()), 2),
-                     "measured_depth_mm": round(float(meas.mean()), 2),
-                     "error_mm_mean": round(float(err.mean()), 3),
-                     "error_mm_rms": round(float(np.sqrt((err ** 2).mean())), 3),
-                     "points": int(ok_core.sum())})
+    rows = accuracy.pothole_depths(xyz, d_true, sc, pots, grooves, f, B, u0, v0)
+    for r in rows:
+        for k in ("true_depth_mm", "measured_depth_mm"):
+            r[k] = round(r[k], 2)
+        for k in ("error_mm_mean", "error_mm_rms"):
+            r[k] = round(r[k], 3)
     allerr = np.array([r["error_mm_mean"] for r in rows])
     return {"report": "accuracy", "workload": w.name, "f_px": f, "baseline_mm": B,
             "potholes_used": len(rows), "potholes_in_scene": len(pots),

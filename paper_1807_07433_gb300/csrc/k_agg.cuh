@@ -89,7 +89,7 @@ __device__ __forceinline__ void load_col8(const __nv_bfloat16 *col, int sl, int,
 // half the copies of CW = 16) where MINB CTAs still fit an SM, else 16; with
 // CW = 16, odd chunks start one pixel earlier, which moves their words to
 // the other half of the banks (the chunk stride is a multiple of 32 words).
-template <int R, int D, typename VT, bool SH = false>
+template <int R, int D, typename VT, bool SH = false, bool BANDED = false>
 struct AggCfg {
     // Lane layout.  A lane holds PX = 2 pixels x 4 output rows x DL = 8
     // disparities: 64 sums, as 32 pairs of disparities, each updated by one
@@ -134,8 +134,14 @@ struct AggCfg {
     static constexpr int SHIFT = shear_shift(CW);  // sheared: odd chunks start a pixel earlier
     static constexpr int BH = shear_bh(CW);        // sheared: pixels of a chunk's box
     static constexpr int CSE = shear_cse(CW);      // sheared: chunk stride (elements)
+    // elements between the cost columns of a ring row: D, except for the
+    // 16-disparity slices of the band kernel, whose 2-D copies widen each
+    // column by 16 bytes (the next disparities, or zeros past the volume's
+    // last): a 16-disparity column spans only 16 banks, and the padding
+    // spreads the pixel groups of a warp over all 32
+    static constexpr int CS = BANDED ? D + (int)(16 / sizeof(VT)) : D;
     // elements of one cost row of the tile
-    static constexpr int RING = SH ? NCH * CSE : TXE * D;
+    static constexpr int RING = SH ? NCH * CSE : TXE * CS;
     // slot stride: RING rounded up to 128 bytes
     static constexpr int RINGS = (int)(((RING * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
     static constexpr int WRING = kAggTY * WS * kAggTX;  // floats per weight slot
@@ -226,9 +232,9 @@ __device__ __forceinline__ float ex2_approx(float x) {   // 2^x, hardware approx
 }
 
 // Shared-memory carve-up of an aggregation CTA (see AggCfg).
-template <int R, int D, typename VT, bool SH = false>
+template <int R, int D, typename VT, bool SH = false, bool BANDED = false>
 struct AggSmem {
-    using C = AggCfg<R, D, VT, SH>;
+    using C = AggCfg<R, D, VT, SH, BANDED>;
     unsigned char *raw;
     __device__ float *epi() const { return reinterpret_cast<float *>(raw); }
     __device__ VT *ring() const { return reinterpret_cast<VT *>(raw); }
@@ -242,8 +248,8 @@ struct AggSmem {
     __device__ int *start() const { return next_slot() + 4; }
 };
 
-template <int R, int D, typename VT, bool SH>
-__device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT, SH> &sm) {
+template <int R, int D, typename VT, bool SH, bool BANDED>
+__device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT, SH, BANDED> &sm) {
     if (threadIdx.x == 0) {
         mbar_init(&sm.bars()[0], 1);
         mbar_init(&sm.bars()[1], 1);
@@ -262,7 +268,7 @@ __device__ __forceinline__ void agg_init_barriers(const AggSmem<R, D, VT, SH> &s
 // WIN: win restricts the WTA and Eq. 12 of each pixel to its window (see
 // AggWin); a compile-time choice, so that the full search keeps its own code.
 template <int R, int D, bool GU8, typename VT, bool BAND = false, bool WIN = BAND, bool SH = false>
-__device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsigned &ph,
+__device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, unsigned &ph,
                                          const VT *__restrict__ vol, int vpitch,
                                          const uint8_t *__restrict__ gl,
                                          int pitch, const float *__restrict__ gf, int W, int H,
@@ -272,7 +278,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
                                          int withhold_last, int x0, int y0,
                                          const void *tmap = nullptr, int dlo = 0,
                                          const AggWin &win = AggWin()) {
-    using C = AggCfg<R, D, VT, SH>;
+    using C = AggCfg<R, D, VT, SH, BAND>;
     float *smem = sm.epi();                      // epilogue view
     VT *ring = sm.ring();                        // [2][TXE][D] cost rows
     float *wring = sm.wring();                   // [2][4][WS][32] weights
@@ -448,7 +454,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
             // taps outer: a cost column (8 disparities) enters per tap
             // column and serves PX pixels x the valid output rows
             const VT *rs = SH ? ring + (j & 1) * C::RINGS + bx * C::CW
-                              : ring + (j & 1) * C::RINGS + bx * D;
+                              : ring + (j & 1) * C::RINGS + bx * C::CS;
             auto body = [&](auto all_rows) {
                 float2 cst[PX + 2 * R][4];
                 auto load_col = [&](int i) {
@@ -461,7 +467,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH> &sm, unsign
                                                     load_one(rs + sh_off[q + 4] + i * C::CW));
                     } else {
                         float c[8];
-                        load_col8(rs + i * D, sl, D, c);
+                        load_col8(rs + i * C::CS, sl, D, c);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) cst[i][q] = make_float2(c[2 * q], c[2 * q + 1]);
                     }
@@ -636,7 +642,8 @@ k_agg_shear(const __grid_constant__ CUtensorMap tmap, int vpitch, const float *_
 // Band kernel of the restricted search: the tile's kBandD-disparity slice
 // [band, band + kBandD) through a 2-D tensor map of the volume.
 template <int R, bool GU8, typename VT>
-__global__ void __launch_bounds__(AggCfg<R, kBandD, VT>::NT, AggCfg<R, kBandD, VT>::MINB)
+__global__ void __launch_bounds__(AggCfg<R, kBandD, VT, false, true>::NT,
+                                  AggCfg<R, kBandD, VT, false, true>::MINB)
 k_agg_band(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__ gl, int pitch,
            const float *__restrict__ gf, int W, int H, float kd, float kr,
            int16_t *__restrict__ lbl, float *__restrict__ dsub, int *__restrict__ err,
@@ -644,7 +651,7 @@ k_agg_band(const __grid_constant__ CUtensorMap tmap, const uint8_t *__restrict__
     const int dlo = win.band[blockIdx.y * gridDim.x + blockIdx.x];
     if (dlo < 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const AggSmem<R, kBandD, VT> sm{smem_raw};
+    const AggSmem<R, kBandD, VT, false, true> sm{smem_raw};
     agg_init_barriers(sm);
     unsigned ph = 0;
     agg_tile<R, kBandD, GU8, VT, true>(sm, ph, nullptr, W, gl, pitch, gf, W, H, kd, kr, lbl, dsub,
@@ -729,7 +736,7 @@ cudaError_t agg_band_launch_t(const CUtensorMap &tmap, const uint8_t *gl, int pi
                               const float *gf, int W, int H, float kd, float kr, int16_t *lbl,
                               float *dsub, const AggDebug &dbg, const AggWin &win,
                               cudaStream_t st) {
-    using C = AggCfg<R, kBandD, VT>;
+    using C = AggCfg<R, kBandD, VT, false, true>;
     const dim3 grid((W + kAggTX - 1) / kAggTX, (H + kAggTY - 1) / kAggTY);
     auto k = gl ? k_agg_band<R, true, VT> : k_agg_band<R, false, VT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -292,7 +292,8 @@ EncodeTiledFn encode_tiled() {
 }
 
 // Tensor map of a cost volume [H][W][D] viewed as [H*W][D], box kBandD
-// disparities x (32 + 2 agg_r) pixels, zeros outside.
+// disparities plus 16 bytes (the band kernel's padded cost columns) x
+// (32 + 2 agg_r) pixels, zeros outside.
 bool encode_volume_map(CUtensorMap *m, void *vol, int vt, int W, int H, int D, int agg_r) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
@@ -301,7 +302,8 @@ bool encode_volume_map(CUtensorMap *m, void *vol, int vt, int W, int H, int D, i
                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)W * H};
     const cuuint64_t strides[1] = {(cuuint64_t)D * sr::vol_elem_bytes(vt)};
-    const cuuint32_t box[2] = {(cuuint32_t)sr::kBandD, (cuuint32_t)(32 + 2 * agg_r)};
+    const cuuint32_t box[2] = {(cuuint32_t)(sr::kBandD + 16 / sr::vol_elem_bytes(vt)),
+                               (cuuint32_t)(32 + 2 * agg_r)};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, dt, 2, vol, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
