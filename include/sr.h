@@ -23,10 +23,14 @@
  *   - All GPU work is queued asynchronously on the stream given to
  *     sr_create (a cudaStream_t passed as void*; NULL = legacy default
  *     stream).  Functions that write host memory synchronise that stream.
- *   - No function aborts, prints or throws.  Every function returns an
- *     sr_status; sr_status_str() names it.  A CUDA error is reported as
- *     SR_ERR_CUDA; the text of the last CUDA error of a context is kept and
- *     returned by sr_last_error().
+ *   - No function aborts or throws.  Every function returns an sr_status;
+ *     sr_status_str() names it.  A CUDA error is reported as SR_ERR_CUDA;
+ *     the text of the last CUDA error of a context is kept and returned by
+ *     sr_last_error().  Nothing is printed unless the environment sets
+ *     SR_LOG_LEVEL (1: errors and device timeouts on stderr; 2: also
+ *     context creation and the batch autotuner's choices).
+ *   - The API calls and the four stages of sr_match push NVTX ranges named
+ *     after them (visible in NVTX-aware profilers; no cost without one).
  *   - Disparities: the search covers residual disparities 0..D-1 in the
  *     transformed (warped) domain; full disparity = residual + alpha0 +
  *     alpha1*v - delta (Sec. II-C).
@@ -269,7 +273,8 @@ sr_status sr_match_batch(sr_ctx *ctx, int n, const sr_pair_desc *pairs);
  * shape (multiset of image sizes, D, radii, volume type, GPU) times the
  * eight candidate schedules of sr_set_batch_schedule on the caller's data
  * and keeps the fastest.  cache_path (nullable) names a file of
- * one JSON object per line that stores the choices across processes;
+ * one JSON object per line that stores the choices across processes (when
+ * NULL, the path in the environment variable SR_TUNE_CACHE, if set);
  * unreadable lines are skipped (defaults used) and reported by
  * sr_last_error.  Disabled: grid factor 1, caller's order. */
 sr_status sr_set_autotune(sr_ctx *ctx, int enable, const char *cache_path);

@@ -436,6 +436,9 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
         return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
     }
     *out = c;
+    SR_LOG(2, "context %dx%d, D %d, NCC %dx%d, bilateral %dx%d, volume type %d on device %d",
+           p.width, p.height, p.max_disp, 2 * p.ncc_radius + 1, 2 * p.ncc_radius + 1,
+           2 * p.agg_radius + 1, 2 * p.agg_radius + 1, (int)p.vol_dtype, c->device);
     return SR_OK;
 }
 
@@ -534,6 +537,7 @@ sr_status sr_synchronize(sr_ctx *c) {
 
 sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                    float *d_disp, int16_t *d_wta_or_null) {
+    NvtxRange nvtx_call("sr_match");
     if (!c || !d_left || !d_right || !d_disp || pitch_bytes < c->p.width) return SR_ERR_INVALID_ARG;
     const sr_params &p = c->p;
     const int W = p.width, H = p.height, D = p.max_disp;
@@ -556,25 +560,34 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     }
     const int WE = W + D - 1;
     SR_TRY(c, mark(), "cudaEventRecord");
-    SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
-                              c->alpha1, c->delta, 0, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                              c->inv_r, c->rowsh, st),
-           "prep");
+    {
+        NvtxRange r("prep");
+        SR_TRY(c, sr::launch_prep(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, c->alpha0,
+                                  c->alpha1, c->delta, 0, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                                  c->inv_r, c->rowsh, st),
+               "prep");
+    }
     SR_TRY(c, mark(), "cudaEventRecord");
-    // one extended reference volume holds both views (target c(u,d) =
-    // extended reference c(u+d,d))
-    SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st, nullptr,
-                             WE),
-           "ncc");
+    {
+        // one extended reference volume holds both views (target c(u,d) =
+        // extended reference c(u+d,d))
+        NvtxRange r("ncc");
+        SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
+                                 c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st,
+                                 nullptr, WE),
+               "ncc");
+    }
     SR_TRY(c, mark(), "cudaEventRecord");
     const sr::AggDebug dbg = agg_debug(c);
     // target view first: the reference-view kernel runs the L-R check and
     // the post-processing in its epilogue, on the finished target labels
-    SR_TRY(c, sr::launch_agg_shear(&c->tmap_x, p.vol_dtype, c->rw, W, H, D, p.agg_radius,
-                                   p.gamma_d, p.gamma_r, c->lbl_r, keep ? c->agg_r : nullptr, dbg,
-                                   st),
-           "agg_tgt");
+    {
+        NvtxRange r("agg_tgt");
+        SR_TRY(c, sr::launch_agg_shear(&c->tmap_x, p.vol_dtype, c->rw, W, H, D, p.agg_radius,
+                                       p.gamma_d, p.gamma_r, c->lbl_r, keep ? c->agg_r : nullptr,
+                                       dbg, st),
+               "agg_tgt");
+    }
     SR_TRY(c, mark(), "cudaEventRecord");
     sr::AggWin post;
     post.post.lbl_r = c->lbl_r;
@@ -582,10 +595,13 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     post.post.wta = d_wta_or_null;
     post.post.rowsh = c->rowsh;
     post.post.lr_thresh = p.lr_thresh;
-    SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D, p.agg_radius,
-                             p.gamma_d, p.gamma_r, c->lbl_l, c->dsub, keep ? c->agg_l : nullptr,
-                             dbg, st, post, WE),
-           "agg_ref");
+    {
+        NvtxRange r("agg_ref");
+        SR_TRY(c, sr::launch_agg(c->vol_l, p.vol_dtype, d_left, pitch_bytes, nullptr, W, H, D,
+                                 p.agg_radius, p.gamma_d, p.gamma_r, c->lbl_l, c->dsub,
+                                 keep ? c->agg_l : nullptr, dbg, st, post, WE),
+               "agg_ref");
+    }
     SR_TRY(c, mark(), "cudaEventRecord");
     c->matched = true;
     c->vol_ext = true;
@@ -598,6 +614,7 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
 sr_status sr_match_rows(sr_ctx *c, const uint8_t *d_left_rows, const uint8_t *d_right_rows,
                         int pitch_bytes, int y0, int y1, float *d_disp_rows,
                         int16_t *d_wta_rows_or_null) {
+    NvtxRange nvtx_call("sr_match_rows");
     if (!c || !d_left_rows || !d_right_rows || !d_disp_rows || pitch_bytes < c->p.width)
         return SR_ERR_INVALID_ARG;
     const sr_params &p = c->p;
@@ -661,6 +678,7 @@ sr_status sr_match_rows(sr_ctx *c, const uint8_t *d_left_rows, const uint8_t *d_
 sr_status sr_match_restricted(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right,
                               int pitch_bytes, const int16_t *d_centre, int radius, float *d_disp,
                               int16_t *d_wta_or_null) {
+    NvtxRange nvtx_call("sr_match_restricted");
     if (!c || !d_left || !d_right || !d_disp || pitch_bytes < c->p.width) return SR_ERR_INVALID_ARG;
     const sr_params &p = c->p;
     const int W = p.width, H = p.height, D = p.max_disp;
@@ -751,6 +769,7 @@ static sr_status ensure_staging(sr_ctx *c) {
 }
 
 sr_status sr_match_host(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right, float *h_disp) {
+    NvtxRange nvtx_call("sr_match_host");
     if (!c || !h_left || !h_right || !h_disp) return SR_ERR_INVALID_ARG;
     const size_t npx = (size_t)c->p.width * c->p.height;
     sr_status s0 = ensure_staging(c);
@@ -771,6 +790,7 @@ sr_status sr_match_host(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right
 
 sr_status sr_match_host_async(sr_ctx *c, const uint8_t *h_left, const uint8_t *h_right,
                               float *h_disp) {
+    NvtxRange nvtx_call("sr_match_host_async");
     if (!c || !h_left || !h_right || !h_disp) return SR_ERR_INVALID_ARG;
     const size_t npx = (size_t)c->p.width * c->p.height;
     sr_status s0 = ensure_staging(c);
@@ -814,6 +834,7 @@ sr_status sr_match_host_async(sr_ctx *c, const uint8_t *h_left, const uint8_t *h
 }
 
 sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {
+    NvtxRange nvtx_call("sr_reconstruct");
     if (!c || !d_disp || !d_xyz) return SR_ERR_INVALID_ARG;
     if (!c->camera) return SR_ERR_STATE;
     SR_TRY(c, sr::launch_xyz(d_disp, c->p.width, c->p.height, c->f_px, c->baseline, c->u0, c->v0,
@@ -825,6 +846,7 @@ sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {
 sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int pitch_bytes,
                         const int16_t *d_dstar, double *h_out3, float *d_grad_left,
                         float *d_grad_right) {
+    NvtxRange nvtx_call("sr_grad_plane");
     if (!c || !d_left || !d_right || !d_dstar || !h_out3 || pitch_bytes < c->p.width)
         return SR_ERR_INVALID_ARG;
     const sr_params &p = c->p;
@@ -868,6 +890,7 @@ sr_status sr_grad_plane(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right
 sr_status sr_fit_alpha(sr_ctx *c, const float *d_disp, int n_hyp, const int32_t *h_pairs,
                        float tau_px, double *h_alpha, int32_t *h_counts, int *h_best,
                        int *h_n_inliers) {
+    NvtxRange nvtx_call("sr_fit_alpha");
     if (!c || !d_disp || !h_pairs || !h_alpha || n_hyp < 1 || n_hyp > (1 << 16) ||
         !(tau_px >= 0.0f) || !isfinite(tau_px))
         return SR_ERR_INVALID_ARG;
@@ -926,6 +949,7 @@ sr_status sr_fit_alpha(sr_ctx *c, const float *d_disp, int n_hyp, const int32_t 
 
 sr_status sr_fit_roll(sr_ctx *c, const float *d_disp, int u_lo, int v_lo, int u_hi, int v_hi,
                       double *h_gamma, double *h_roll, int *h_n) {
+    NvtxRange nvtx_call("sr_fit_roll");
     if (!c || !d_disp || !h_gamma || !h_roll) return SR_ERR_INVALID_ARG;
     const int W = c->p.width, H = c->p.height;
     u_lo = std::max(u_lo, 0); v_lo = std::max(v_lo, 0);

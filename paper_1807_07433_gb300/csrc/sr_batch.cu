@@ -33,6 +33,7 @@
 // defaults are used) and reported through sr_last_error.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -412,7 +413,9 @@ sr_status sr_set_autotune(sr_ctx *c, int enable, const char *cache_path) {
     }
     SrBatch *b = c->batch;
     b->tune = enable != 0;
-    b->cache_path = cache_path ? cache_path : "";
+    // no path given: the SR_TUNE_CACHE environment variable, if set
+    const char *env = getenv("SR_TUNE_CACHE");
+    b->cache_path = cache_path ? cache_path : (env ? env : "");
     b->tuned.clear();
     b->cache_bad = false;
     load_cache(b, c);
@@ -489,6 +492,7 @@ sr_status sr_match_batch(sr_ctx *c, int n, const sr_pair_desc *pairs) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             b->tuned[key] = variant;
+            SR_LOG(2, "batch autotuner: variant %d for %s", variant, key.c_str());
             append_cache(b, key, variant, b->tune_ms);
         }
     }

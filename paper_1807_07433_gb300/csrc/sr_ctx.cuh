@@ -2,7 +2,9 @@
 // error helpers shared by the ABI translation units.  Not installed.
 #pragma once
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include "../../include/sr.h"
 #include "sr_internal.cuh"
@@ -80,8 +82,37 @@ struct sr_ctx {
 
 namespace {
 
+// Host-side diagnostics on stderr, off unless the environment sets
+// SR_LOG_LEVEL: 1 = errors and device timeouts, 2 = also context creation
+// and the batch autotuner's choices.  Read once per process.
+inline int sr_log_level() {
+    static const int level = [] {
+        const char *e = getenv("SR_LOG_LEVEL");
+        return e ? atoi(e) : 0;
+    }();
+    return level;
+}
+#define SR_LOG(level, ...)                                   \
+    do {                                                     \
+        if (sr_log_level() >= (level)) {                     \
+            fprintf(stderr, "sr: " __VA_ARGS__);             \
+            fputc('\n', stderr);                             \
+        }                                                    \
+    } while (0)
+
+// An NVTX range on the calling thread for the lifetime of the object: the
+// API calls and the stages of a match show up by name in NVTX-aware tools
+// (nothing is recorded when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 inline sr_status fail_cuda(sr_ctx *c, cudaError_t e, const char *what) {
     if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+    SR_LOG(1, "%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
 }
 
@@ -99,6 +130,7 @@ inline sr_status take_device_error(sr_ctx *c) {
     if (h == 0) return SR_OK;
     cudaMemset(c->d_err, 0, sizeof(int));
     snprintf(c->err, sizeof(c->err), "a bounded device wait for a cost-row copy ran out");
+    SR_LOG(1, "%s", c->err);
     return SR_ERR_TIMEOUT;
 }
 

@@ -220,3 +220,16 @@ def test_batch_at_the_mixed_workload_sizes(vt):
         sr.sr_set_autotune(m.ctx, True)
         _same(_batch(m.ctx, pairs), want)
         _same(_batch(m.ctx, pairs, order=[3, 1, 0, 2]), want)
+
+
+def test_autotune_cache_path_from_environment(tmp_path, monkeypatch):
+    """sr_set_autotune without a path takes SR_TUNE_CACHE from the environment."""
+    from paper_1807_07433_gb300 import sr
+    cache = tmp_path / "env_tune.jsonl"
+    monkeypatch.setenv("SR_TUNE_CACHE", str(cache))
+    p = _pairs(800)
+    with _ctx() as m:
+        sr.sr_set_autotune(m.ctx, True)
+        _same(_batch(m.ctx, p), _single(p, 0))
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and '"variant"' in lines[0]

@@ -357,3 +357,24 @@ def test_large_frame_sampled_pixels():
         np.isfinite(o["dfull"]) & np.isfinite(g["dfull"][vs, us])
     np.testing.assert_allclose(g["dfull"][vs, us][sharp], o["dfull"][sharp], rtol=0,
                                atol=TOL_DSUB)
+
+
+def test_log_level_from_environment():
+    """SR_LOG_LEVEL=2 makes the library report context creation on stderr;
+    by default it prints nothing."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1807_07433_gb300 import sr\n"
+            "m = sr.Matcher(64, 32, 16, 2, 2, 3.0, 10.0); m.close()\n" % root)
+    env = dict(os.environ, SR_LOG_LEVEL="2")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "sr: context 64x32, D 16" in r.stderr
+    env.pop("SR_LOG_LEVEL")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and "sr:" not in r.stderr
