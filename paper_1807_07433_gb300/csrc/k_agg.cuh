@@ -20,18 +20,20 @@
 //     128-bit load gives one tap's weight for four adjacent pixels.  Each
 //     weight is computed exactly once, and shared memory stays ~36 KB per
 //     CTA, so four CTAs (16 warps) fit on an SM;
-//   * lane = 8 disparities of a block of 2 x 4 pixels; the D/8 lanes of a
-//     pixel group read the same weights (a broadcast) and each a different
-//     part of a cost column (two 16-byte loads, conflict-free);
-//   * each thread accumulates 2 x 4 pixels x 8 disparities = 64 sums, held as
-//     32 pairs of disparities that one paired multiply-add (fma.rn.f32x2)
-//     updates per tap, the weight paired with itself.  Tap columns are the
-//     outer loop: per tap column one new cost column enters the thread's
-//     sliding window and serves both pixels and every output row that uses
-//     the source row (32 independent paired multiply-adds);
+//   * lane = 4 disparities of a block of 4 x 4 pixels (8 disparities of
+//     2 x 4 pixels for FP32 costs at D = 64); the lanes of a pixel group
+//     read the same weights (a broadcast) and together one cost column
+//     (16-byte loads, conflict-free);
+//   * each thread accumulates 64 sums, held as 32 pairs of disparities that
+//     one paired multiply-add (fma.rn.f32x2) updates per tap, the weight
+//     paired with itself.  Tap columns are the outer loop: per tap column
+//     one new cost column enters the thread's sliding window and serves the
+//     lane's pixels and every output row that uses the source row (32
+//     independent paired multiply-adds);
 //   * epilogue: the sums are transposed through shared memory (over the
-//     rings) so that each lane scans the D costs of one pixel: argmax (ties
-//     to the smallest d), then Eq. 12 on the neighbours of the winner.  The
+//     rings; 16-byte stores, rows of D + 4) so that each lane scans the D
+//     costs of one pixel, four per load: argmax (ties to the smallest d),
+//     then Eq. 12 on the neighbours of the winner.  The
 //     normalisation by sum_k w_k is a positive per-pixel scale, which
 //     changes neither the argmax nor the parabola vertex, so it is applied
 //     only when the aggregated volume is exported.
@@ -46,40 +48,24 @@ namespace sr {
 
 constexpr int kAggTX = 32, kAggTY = 4, kAggPix = kAggTX * kAggTY;
 
-// Disparity of value k (0..7) held by lane sl of a pixel group in the layout
-// with 8 disparities per lane: for FP32 costs, k < 4 from the first half of
-// the disparities and k >= 4 from the second (two 16-byte loads that together
-// cover a cost column without bank conflicts); for 16-bit costs, 8
-// consecutive disparities (one 16-byte load).
-template <int D, typename VT>
-__device__ __forceinline__ int lane_disp8(int sl, int k) {
-    if (sizeof(VT) == 4) return (k >> 2) * (D / 2) + 4 * sl + (k & 3);
-    return 8 * sl + k;
+// The 4 costs of lane sl of a pixel group in the cost column at col (layout
+// [col][D]): disparities 4 sl .. 4 sl + 3, one 16-byte (FP32) or 8-byte
+// (16-bit) load, widened to FP32.
+__device__ __forceinline__ float4 load_col4(const float *col, int sl) {
+    return *reinterpret_cast<const float4 *>(col + 4 * sl);
 }
-// The 8 costs of lane sl in the cost column at col (layout [col][D]).
-__device__ __forceinline__ void load_col8(const float *col, int sl, int D, float *c) {
-    const float4 a = *reinterpret_cast<const float4 *>(col + 4 * sl);
-    const float4 b = *reinterpret_cast<const float4 *>(col + D / 2 + 4 * sl);
-    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
-    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+__device__ __forceinline__ float4 load_col4(const __half *col, int sl) {
+    const uint2 q = *reinterpret_cast<const uint2 *>(col + 4 * sl);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    return make_float4(a.x, a.y, b.x, b.y);
 }
-template <typename H2>
-__device__ __forceinline__ void widen8(const uint4 &q, float *c) {
-    const H2 *h = reinterpret_cast<const H2 *>(&q);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float2 f;
-        if constexpr (std::is_same<H2, __half2>::value) f = __half22float2(h[i]);
-        else f = __bfloat1622float2(h[i]);
-        c[2 * i] = f.x;
-        c[2 * i + 1] = f.y;
-    }
-}
-__device__ __forceinline__ void load_col8(const __half *col, int sl, int, float *c) {
-    widen8<__half2>(*reinterpret_cast<const uint4 *>(col + 8 * sl), c);
-}
-__device__ __forceinline__ void load_col8(const __nv_bfloat16 *col, int sl, int, float *c) {
-    widen8<__nv_bfloat162>(*reinterpret_cast<const uint4 *>(col + 8 * sl), c);
+__device__ __forceinline__ float4 load_col4(const __nv_bfloat16 *col, int sl) {
+    // a bfloat16 is the upper half of the FP32 word of equal value: one
+    // shift or mask per element, no conversion instruction
+    const uint2 q = *reinterpret_cast<const uint2 *>(col + 4 * sl);
+    return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u),
+                       __uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u));
 }
 
 // SH: the tile reads a cost row sheared, pixel u at disparity d from column
@@ -91,16 +77,26 @@ __device__ __forceinline__ void load_col8(const __nv_bfloat16 *col, int sl, int,
 // the other half of the banks (the chunk stride is a multiple of 32 words).
 template <int R, int D, typename VT, bool SH = false, bool BANDED = false>
 struct AggCfg {
-    // Lane layout.  A lane holds PX = 2 pixels x 4 output rows x DL = 8
+    // Lane layout.  A lane holds PX = 4 pixels x 4 output rows x DL = 4
     // disparities: 64 sums, as 32 pairs of disparities, each updated by one
-    // paired multiply-add (fma.rn.f32x2) per tap.  Shared memory, not the FMA
-    // pipe, sets the pace of this loop, so the layout minimises shared-memory
-    // traffic per multiply-add for 64 sums: a weight pair (8 bytes) feeds 16
-    // multiply-adds and a cost column (8 disparities, 32 bytes) 2 pixels x 4
-    // rows.  Contiguous rows read a cost column with two 16-byte loads; the
-    // sheared rows of the target view read the 8 disparities of a pixel from
-    // the diagonal of their chunks, one element each.
-    static constexpr int DL = 8;
+    // paired multiply-add (fma.rn.f32x2) per tap, the weight paired with
+    // itself.  Shared memory sets the pace of this loop, and its cost is
+    // wavefronts, not lane bytes: the D/4 lanes of a pixel group read one
+    // cost column together (D x 4 bytes, the fewest wavefronts a column can
+    // take), and the lanes of a group share each weight load (a broadcast:
+    // one wavefront for the warp's float4 of 4 pixels).  Per tap column a
+    // lane loads one cost column (4 disparities) and one float4 of weights per
+    // output row, which feed 32 multiply-adds.  The sheared rows of the
+    // target view read the 4 disparities of a pixel from the diagonal of
+    // their chunks, one element each.
+    //
+    // FP32 costs at D = 64 keep an earlier layout of 8 disparities x 2
+    // pixels (disparities 4 sl.. and D/2 + 4 sl.., two 16-byte loads per
+    // column): it runs the target view 2 % faster there, with fewer
+    // registers, although it takes 40 % more wavefronts per row.  For D = 16
+    // and 32 that layout conflicts on every column load, and for 16-bit
+    // costs it converts twice as many elements per multiply-add.
+    static constexpr int DL = (sizeof(VT) == 4 && D == 64 && !BANDED) ? 8 : 4;
     static constexpr int SLOTS = D / DL;           // lanes per pixel group
     static constexpr int G = 32 / SLOTS;           // pixel groups per warp
     static constexpr int PX = 16 / DL;             // pixel columns of a group
@@ -119,10 +115,13 @@ struct AggCfg {
         return (int)(((shear_bh(cw) * cw * sizeof(VT) + 127) / 128 * 128) / sizeof(VT));
     }
     // shared memory of a CTA whose cost-ring slot holds ring elements
+    // epilogue: a pixel's D sums, rows padded to a multiple of 16 bytes so
+    // that a lane stores its 4 disparities, and the scan loads 4, at once
+    static constexpr int EPS = D + 4;
     static constexpr size_t single_for(int ring) {
         const size_t rings = ((size_t)ring * sizeof(VT) + 127) / 128 * 128;
         const size_t ringsb = 2 * rings + (NW > 1 ? 2 : 1) * (size_t)(kAggTY * WS * kAggTX) * sizeof(float);
-        const size_t epib = (size_t)kAggPix * (D + 1) * sizeof(float);
+        const size_t epib = (size_t)kAggPix * EPS * sizeof(float);
         const size_t uni = ((ringsb > epib ? ringsb : epib) + 15) / 16 * 16;
         return uni + sizeof(float) * (((size_t)TYE * TXE + 3) / 4 * 4 + kAggPix) +
                2 * sizeof(unsigned long long) + sizeof(int) * 4;
@@ -153,7 +152,7 @@ struct AggCfg {
     // epilogue transpose), guide tile, weight sums, two mbarriers
     static constexpr size_t RINGB = 2 * (size_t)RINGS * sizeof(VT);
     static constexpr size_t RINGSB = RINGB + WSL * (size_t)WRING * sizeof(float);
-    static constexpr size_t EPIB = (size_t)kAggPix * (D + 1) * sizeof(float);
+    static constexpr size_t EPIB = (size_t)kAggPix * EPS * sizeof(float);
     static constexpr size_t UNIONB = ((RINGSB > EPIB ? RINGSB : EPIB) + 15) / 16 * 16;
     static constexpr int GUIDE = TYE * TXE;
     // (+ the batched kernel's work-list prefix and next-item slot, last, so
@@ -407,20 +406,23 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
     const int sl = lane % C::SLOTS, grp = lane / C::SLOTS;
     const int bcol = warp * C::G + grp;          // block column of PX pixels
     const int bx = bcol * PX;                    // first tile column of the block
-    // sheared rows with 8 disparities per lane: pair q of the lane holds
-    // disparities m_q and m_q + D/2, m_q = (sl + SLOTS q + 8 grp) mod D/2, so
-    // that the 32 lanes of a warp read 32 different banks for D = 64; the
-    // element of disparity d for tile pixel i sits at offset
-    // (d / CW) CSE + (i + d % CW + SHIFT ((d / CW) & 1)) CW + d % CW
-    int sh_m[4] = {0, 0, 0, 0}, sh_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // sheared rows: pair q of the lane holds disparities m_q and m_q + D/2,
+    // m_q = (sl + SLOTS q + c grp) mod D/2, the x half of the pair being
+    // m_q + D/2 in odd groups (sh_hx); with c = D^2/256 and the swap (4
+    // disparities per lane), or c = 8 and no swap (8 per lane, D = 64), the
+    // 32 lanes of a warp load from 32 different banks for D = 32 and 64 (2
+    // per bank for D = 16).  The element of disparity d for tile pixel i sits
+    // at offset (d / CW) CSE + (i + d % CW + SHIFT ((d / CW) & 1)) CW + d % CW
+    int sh_m[DL / 2] = {}, sh_off[DL] = {}, sh_hx = 0;
     if constexpr (SH) {
+        sh_hx = DL == 4 ? (grp & 1) : 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            sh_m[q] = (sl + C::SLOTS * q + 8 * grp) % (D / 2);
+        for (int q = 0; q < DL / 2; ++q) {
+            sh_m[q] = (sl + C::SLOTS * q + (DL == 4 ? D * D / 256 : 8) * grp) % (D / 2);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int d = sh_m[q] + h * (D / 2), c = d / C::CW, m = d % C::CW;
-                sh_off[q + 4 * h] = c * C::CSE + (m + C::SHIFT * (c & 1)) * C::CW + m;
+            for (int h = 0; h < 2; ++h) {   // h = 0: the pair's x element
+                const int d = sh_m[q] + (h ^ sh_hx) * (D / 2), c = d / C::CW, m = d % C::CW;
+                sh_off[q + (DL / 2) * h] = c * C::CSE + (m + C::SHIFT * (c & 1)) * C::CW + m;
             }
         }
     }
@@ -451,25 +453,32 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
         if (y >= 0 && y < H) {
             mbar_wait(bars + (j & 1), (ph >> (j & 1)) & 1u, wait_cycles, err);
             const float *ws = wring + (j % C::WSL) * C::WRING + bx;
-            // taps outer: a cost column (8 disparities) enters per tap
+            // taps outer: a cost column (4 disparities) enters per tap
             // column and serves PX pixels x the valid output rows
             const VT *rs = SH ? ring + (j & 1) * C::RINGS + bx * C::CW
                               : ring + (j & 1) * C::RINGS + bx * C::CS;
             auto body = [&](auto all_rows) {
-                float2 cst[PX + 2 * R][4];
+                float2 cst[PX + 2 * R][DL / 2];
                 auto load_col = [&](int i) {
                     if constexpr (SH) {
-                        // pair q: disparities sh_m[q] and sh_m[q] + D/2, on
-                        // the diagonal of their chunks (offsets sh_off)
+                        // pair q: the diagonal elements at sh_off[q] (x)
+                        // and sh_off[q + DL/2] (y)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
+                        for (int q = 0; q < DL / 2; ++q)
                             cst[i][q] = make_float2(load_one(rs + sh_off[q] + i * C::CW),
-                                                    load_one(rs + sh_off[q + 4] + i * C::CW));
+                                                    load_one(rs + sh_off[q + DL / 2] + i * C::CW));
+                    } else if constexpr (DL == 8) {
+                        // disparities 4 sl .. 4 sl + 3 and D/2 + 4 sl .. D/2 + 4 sl + 3
+                        const float4 a = load_col4(rs + i * C::CS, sl);
+                        const float4 b = load_col4(rs + i * C::CS + D / 2, sl);
+                        cst[i][0] = make_float2(a.x, a.y);
+                        cst[i][1] = make_float2(a.z, a.w);
+                        cst[i][2] = make_float2(b.x, b.y);
+                        cst[i][3] = make_float2(b.z, b.w);
                     } else {
-                        float c[8];
-                        load_col8(rs + i * C::CS, sl, D, c);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) cst[i][q] = make_float2(c[2 * q], c[2 * q + 1]);
+                        const float4 c = load_col4(rs + i * C::CS, sl);
+                        cst[i][0] = make_float2(c.x, c.y);
+                        cst[i][1] = make_float2(c.z, c.w);
                     }
                 };
 #pragma unroll
@@ -480,15 +489,26 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
 #pragma unroll
                     for (int py = 0; py < kAggTY; ++py) {
                         if (decltype(all_rows)::value || (unsigned)(j - py) < (unsigned)C::WS) {
-                            // the weights of the lane's two pixels, each
-                            // paired with itself for the paired multiply-add
-                            const float2 w2 = *reinterpret_cast<const float2 *>(
-                                ws + (py * C::WS + dx) * kAggTX);
-                            const float2 w[PX] = {make_float2(w2.x, w2.x), make_float2(w2.y, w2.y)};
+                            // the weights of the lane's pixels, each paired
+                            // with itself for the paired multiply-add
+                            float2 w[PX];
+                            if constexpr (PX == 2) {
+                                const float2 w2 = *reinterpret_cast<const float2 *>(
+                                    ws + (py * C::WS + dx) * kAggTX);
+                                w[0] = make_float2(w2.x, w2.x);
+                                w[1] = make_float2(w2.y, w2.y);
+                            } else {
+                                const float4 w4 = *reinterpret_cast<const float4 *>(
+                                    ws + (py * C::WS + dx) * kAggTX);
+                                w[0] = make_float2(w4.x, w4.x);
+                                w[1] = make_float2(w4.y, w4.y);
+                                w[2] = make_float2(w4.z, w4.z);
+                                w[3] = make_float2(w4.w, w4.w);
+                            }
 #pragma unroll
                             for (int px = 0; px < PX; ++px)
 #pragma unroll
-                                for (int q = 0; q < 4; ++q)
+                                for (int q = 0; q < DL / 2; ++q)
                                     acc[py][px][q] = __ffma2_rn(w[px], cst[px + dx][q], acc[py][px][q]);
                         }
                     }
@@ -520,24 +540,25 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             wsum[py * kAggTX + px] = s > 0.0f ? s : 1.0f;
         }
     }
-    float *E = smem + warp * (C::PPG * C::G) * (D + 1);     // this warp's pixels x D
+    float *E = smem + warp * (C::PPG * C::G) * C::EPS;     // this warp's pixels x D
 #pragma unroll
     for (int py = 0; py < kAggTY; ++py)
 #pragma unroll
         for (int px = 0; px < PX; ++px) {
-            float *e = E + (grp * C::PPG + py * PX + px) * (D + 1);
+            float *e = E + (grp * C::PPG + py * PX + px) * C::EPS;
             if constexpr (SH) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    e[sh_m[q]] = acc[py][px][q].x;
-                    e[sh_m[q] + D / 2] = acc[py][px][q].y;
+                for (int q = 0; q < DL / 2; ++q) {
+                    e[sh_m[q] + sh_hx * (D / 2)] = acc[py][px][q].x;
+                    e[sh_m[q] + (1 - sh_hx) * (D / 2)] = acc[py][px][q].y;
                 }
             } else {
+                // quad k of the lane: disparities 4 sl + k D/2 .. + 3
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    e[lane_disp8<D, VT>(sl, 2 * q)] = acc[py][px][q].x;
-                    e[lane_disp8<D, VT>(sl, 2 * q + 1)] = acc[py][px][q].y;
-                }
+                for (int k = 0; k < DL / 4; ++k)
+                    *reinterpret_cast<float4 *>(e + 4 * sl + k * (D / 2)) =
+                        make_float4(acc[py][px][2 * k].x, acc[py][px][2 * k].y,
+                                    acc[py][px][2 * k + 1].x, acc[py][px][2 * k + 1].y);
             }
         }
     __syncthreads();
@@ -546,17 +567,24 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
         const int tpx = (warp * C::G + g) * PX + px;
         const int u = x0 + tpx, v = y0 + py;
         if (u >= W || v >= H) continue;
-        const float *e = E + pw * (D + 1);
+        const float *e = E + pw * C::EPS;
         const size_t o = (size_t)v * W + u;
         // search window in slice indices: 0..D-1, or the pixel's window
         int lo = 0, hi = D - 1;
         int best = 0;
         float cb = e[0];
         if (!WIN) {
-#pragma unroll 8
-            for (int d = 1; d < D; ++d) {
-                const float c = e[d];
+            // four sums per load, in disparity order (ties keep the smaller d)
+            auto take = [&](float c, int d) {
                 if (c > cb) { cb = c; best = d; }
+            };
+#pragma unroll 4
+            for (int k = 0; k < D / 4; ++k) {
+                const float4 c = *reinterpret_cast<const float4 *>(e + 4 * k);
+                if (k > 0) take(c.x, 4 * k);
+                take(c.y, 4 * k + 1);
+                take(c.z, 4 * k + 2);
+                take(c.w, 4 * k + 3);
             }
         } else {
             int cc = win.centre ? win.centre[o] : win.centre_const;
@@ -599,7 +627,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             if (u >= W || v >= H) continue;
             const float sc = 1.0f / wsum[py * kAggTX + tpx];
             for (int d = lane; d < D; d += 32)
-                agg[((size_t)v * W + u) * D + d] = E[pw * (D + 1) + d] * sc;
+                agg[((size_t)v * W + u) * D + d] = E[pw * C::EPS + d] * sc;
         }
     }
 }

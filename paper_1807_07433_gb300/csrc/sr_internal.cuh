@@ -27,13 +27,17 @@ __device__ __forceinline__ float2 load_pair(const float *p) {
 __device__ __forceinline__ float2 load_pair(const __half *p) {
     return __half22float2(*reinterpret_cast<const __half2 *>(p));
 }
+// (a bfloat16 is the upper half of the FP32 word of equal value)
 __device__ __forceinline__ float2 load_pair(const __nv_bfloat16 *p) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    const unsigned w = *reinterpret_cast<const unsigned *>(p);
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 // One stored cost, widened to FP32.
 __device__ __forceinline__ float load_one(const float *p) { return *p; }
 __device__ __forceinline__ float load_one(const __half *p) { return __half2float(*p); }
-__device__ __forceinline__ float load_one(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float load_one(const __nv_bfloat16 *p) {
+    return __uint_as_float((unsigned)*reinterpret_cast<const unsigned short *>(p) << 16);
+}
 __device__ __forceinline__ void store8(float *p, const float *v) {
     reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
     reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
