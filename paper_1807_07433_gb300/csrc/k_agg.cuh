@@ -90,13 +90,14 @@ struct AggCfg {
     // target view read the 4 disparities of a pixel from the diagonal of
     // their chunks, one element each.
     //
-    // FP32 costs at D = 64 keep an earlier layout of 8 disparities x 2
-    // pixels (disparities 4 sl.. and D/2 + 4 sl.., two 16-byte loads per
-    // column): it runs the target view 2 % faster there, with fewer
-    // registers, although it takes 40 % more wavefronts per row.  For D = 16
-    // and 32 that layout conflicts on every column load, and for 16-bit
-    // costs it converts twice as many elements per multiply-add.
-    static constexpr int DL = (sizeof(VT) == 4 && D == 64 && !BANDED) ? 8 : 4;
+    // FP32 costs at D = 64, and in the band kernel's padded 16-disparity
+    // slices, keep an earlier layout of 8 disparities x 2 pixels
+    // (disparities 4 sl.. and D/2 + 4 sl.., two 16-byte loads per column):
+    // it runs the target view 2 % and the band kernel 2 % faster, with fewer
+    // registers, although it takes 40 % more wavefronts per row.  For
+    // unpadded D = 16 and 32 that layout conflicts on every column load, and
+    // for 16-bit costs it converts twice as many elements per multiply-add.
+    static constexpr int DL = (sizeof(VT) == 4 && (D == 64 || BANDED)) ? 8 : 4;
     static constexpr int SLOTS = D / DL;           // lanes per pixel group
     static constexpr int G = 32 / SLOTS;           // pixel groups per warp
     static constexpr int PX = 16 / DL;             // pixel columns of a group
@@ -116,8 +117,10 @@ struct AggCfg {
     }
     // shared memory of a CTA whose cost-ring slot holds ring elements
     // epilogue: a pixel's D sums, rows padded to a multiple of 16 bytes so
-    // that a lane stores its 4 disparities, and the scan loads 4, at once
-    static constexpr int EPS = D + 4;
+    // that a lane stores its 4 disparities, and the scan loads 4, at once;
+    // the band kernel, whose windows are a few disparities wide, keeps odd
+    // rows (scalar stores and loads, 1 % faster there)
+    static constexpr int EPS = BANDED ? D + 1 : D + 4;
     static constexpr size_t single_for(int ring) {
         const size_t rings = ((size_t)ring * sizeof(VT) + 127) / 128 * 128;
         const size_t ringsb = 2 * rings + (NW > 1 ? 2 : 1) * (size_t)(kAggTY * WS * kAggTX) * sizeof(float);
@@ -555,10 +558,19 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             } else {
                 // quad k of the lane: disparities 4 sl + k D/2 .. + 3
 #pragma unroll
-                for (int k = 0; k < DL / 4; ++k)
-                    *reinterpret_cast<float4 *>(e + 4 * sl + k * (D / 2)) =
-                        make_float4(acc[py][px][2 * k].x, acc[py][px][2 * k].y,
-                                    acc[py][px][2 * k + 1].x, acc[py][px][2 * k + 1].y);
+                for (int k = 0; k < DL / 4; ++k) {
+                    float *q4 = e + 4 * sl + k * (D / 2);
+                    if constexpr (C::EPS % 4 == 0) {
+                        *reinterpret_cast<float4 *>(q4) =
+                            make_float4(acc[py][px][2 * k].x, acc[py][px][2 * k].y,
+                                        acc[py][px][2 * k + 1].x, acc[py][px][2 * k + 1].y);
+                    } else {
+                        q4[0] = acc[py][px][2 * k].x;
+                        q4[1] = acc[py][px][2 * k].y;
+                        q4[2] = acc[py][px][2 * k + 1].x;
+                        q4[3] = acc[py][px][2 * k + 1].y;
+                    }
+                }
             }
         }
     __syncthreads();
@@ -573,7 +585,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
         int lo = 0, hi = D - 1;
         int best = 0;
         float cb = e[0];
-        if (!WIN) {
+        if constexpr (!WIN) {
             // four sums per load, in disparity order (ties keep the smaller d)
             auto take = [&](float c, int d) {
                 if (c > cb) { cb = c; best = d; }
@@ -594,9 +606,18 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             if (hi < lo) hi = lo;
             best = lo;
             cb = e[lo];
-            for (int d = lo + 1; d <= hi; ++d) {
-                const float c = e[d];
-                if (c > cb) { cb = c; best = d; }
+            // the aligned quads that cover the window, in disparity order
+            if constexpr (C::EPS % 4 != 0) {
+                for (int d = lo + 1; d <= hi; ++d)
+                    if (e[d] > cb) { cb = e[d]; best = d; }
+            } else for (int k = lo >> 2; k <= hi >> 2; ++k) {
+                const float4 c = *reinterpret_cast<const float4 *>(e + 4 * k);
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int d = 4 * k + t;
+                    if (d > lo && d <= hi && cv[t] > cb) { cb = cv[t]; best = d; }
+                }
             }
         }
         lbl[o] = (int16_t)(best + dlo);
