@@ -55,7 +55,9 @@ typedef enum {
     SR_ERR_OOM = 3,           /* device or host allocation failed */
     SR_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     SR_ERR_STATE = 5,         /* call out of order (e.g. no camera set) */
-    SR_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+    SR_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    SR_ERR_BOUNDS = 7         /* bounds-checked build: an index fell outside its
+                                 buffer (see sr_bounds_report) */
 } sr_status;
 
 /* Storage type of the staged cost volumes.  All arithmetic is FP32: NCC
@@ -246,6 +248,26 @@ sr_status sr_match_noalloc(const sr_params *params, double alpha0, double alpha1
  * Errors: SR_ERR_CUDA. */
 sr_status sr_noalloc_status(void *cuda_stream);
 
+/* Bounds-checked builds (libsr_check.so, compiled with SR_BOUNDS_CHECK).
+ * Every checked index of the match-path kernels -- warp and block statistics
+ * (Sec. II-A, Eqs. 4-5), NCC (Eq. 3), aggregation (Eqs. 8-12, including its
+ * cost-row copies and shared-memory tiles), L-R check and post-processing
+ * (Eq. 11, Sec. II-C), reconstruction (Sec. II-D) -- that falls outside its
+ * buffer is recorded, the first per launch (site number, index, source
+ * file), and its access is skipped; the call that launched the kernel then
+ * returns SR_ERR_BOUNDS.  Launches inside stream capture are checked at the
+ * next plain launch of the same kernel file.  The arithmetic is that of the
+ * release build, so results are bit-identical where no index is out of range.
+ *
+ * sr_bounds_report copies the first offence recorded since the last report
+ * into *site, *index and unit (unit_len bytes, NUL-terminated), the number
+ * of offences into *count, and clears the record; any pointer may be NULL.
+ * Returns SR_OK when none was recorded, SR_ERR_BOUNDS when one was, and
+ * SR_ERR_UNSUPPORTED in a release build.  Site numbers: 1xx NCC, 2xx
+ * aggregation, 3xx per-pixel kernels.  Thread-safe; process-wide. */
+sr_status sr_bounds_report(int *site, long long *index, char *unit, int unit_len,
+                           long long *count);
+
 /* One stereo pair of a batch (all pointers device pointers owned by the
  * caller; layouts as for sr_match). */
 typedef struct {
@@ -402,6 +424,11 @@ sr_status sr_get_buffer(sr_ctx *ctx, sr_buffer which, void *dst, size_t *bytes_i
 #define SR_DEBUG_KEEP_AGG 1
 #define SR_DEBUG_WITHHOLD_ROW 2
 #define SR_DEBUG_NO_BAND 4       /* sr_match_restricted: every tile runs the full-D kernel */
+/* SR_DEBUG_BOUNDS_SELFTEST: in a bounds-checked build, each sr_reconstruct
+ * records one offence at site 399 (index -1) without any memory access, so
+ * that the call returns SR_ERR_BOUNDS and sr_bounds_report reports it; no
+ * effect in a release build. */
+#define SR_DEBUG_BOUNDS_SELFTEST 8
 sr_status sr_set_debug(sr_ctx *ctx, int flags);
 
 /* Wait for the context's queued work.  Device-side waits are bounded; when

@@ -20,6 +20,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(ROOT, "_build", "sr")
 LIB = os.path.join(PKG, "libsr.so")
+# bounds-checked build (SR_BOUNDS_CHECK: checked indices, sr_bounds_report);
+# built on request, not by build()
+OBJ_CHECK = os.path.join(ROOT, "_build", "sr_check")
+LIB_CHECK = os.path.join(PKG, "libsr_check.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -46,19 +50,22 @@ def _compile(src: str, obj: str, extra: list[str]) -> tuple[str, str]:
     return src, r.stderr
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    """Compile every translation unit under csrc/ and link libsr.so; return its path."""
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None,
+          check: bool = False) -> str:
+    """Compile every translation unit under csrc/ and link libsr.so (with
+    check=True: the bounds-checked libsr_check.so); return its path."""
+    obj_dir, lib = (OBJ_CHECK, LIB_CHECK) if check else (OBJ, LIB)
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_t = _headers_mtime()
     todo, objs = [], []
     for s in srcs:
-        o = os.path.join(OBJ, os.path.splitext(os.path.basename(s))[0] + ".o")
+        o = os.path.join(obj_dir, os.path.splitext(os.path.basename(s))[0] + ".o")
         objs.append(o)
         if force or verbose_ptxas or not os.path.exists(o) or \
                 os.path.getmtime(o) < max(os.path.getmtime(s), hdr_t):
             todo.append((s, o))
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DSR_BOUNDS_CHECK"] if check else [])
     logs = []
     if todo:
         n = jobs or min(len(todo), os.cpu_count() or 4)
@@ -68,15 +75,16 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if verbose_ptxas:
         for src, err in logs:
             sys.stderr.write(f"== {os.path.basename(src)}\n{err}")
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv,
+                check="--check" in sys.argv))

@@ -307,6 +307,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
         if (BAND) {
             // the whole box: pixels beyond the row's ends come from the
             // neighbouring rows (or are zeros) and meet zero weights
+            if (!SR_CHECK((dlo * (int)sizeof(VT)) & 15, 1, 201)) {   // x on a 16-byte boundary
+                mbar_arrive(bar);
+                return;
+            }
             mbar_arrive_expect_tx(bar, (unsigned)(C::RING * sizeof(VT)));
             tma_load_2d(ring + (j & 1) * C::RINGS, tmap, dlo, y * W + x0 - R, bar);
             return;
@@ -317,6 +321,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             // 16c + m sits in box row i + m + (c & 1).  As for BAND, columns
             // beyond the row's ends come from the neighbouring rows (or are
             // zeros) and meet zero weights.
+            if (!SR_CHECK(C::NCH * C::CSE, C::RINGS + 1, 202)) {   // boxes within the slot
+                mbar_arrive(bar);
+                return;
+            }
             mbar_arrive_expect_tx(bar, (unsigned)(C::NCH * C::BH * C::CW * sizeof(VT)));
 #pragma unroll
             for (int c = 0; c < C::NCH; ++c)
@@ -326,6 +334,12 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
         }
         VT *dst = ring + (j & 1) * C::RINGS + (xs - (x0 - R)) * D;
         const VT *src = vol + ((size_t)y * vpitch + xs) * D;
+        // the copy stays inside its slot and inside the volume row
+        if (!SR_CHECK((xe - (x0 - R)) * D - 1, C::RINGS, 203) || !SR_CHECK(xe - 1, vpitch, 203) ||
+            !SR_CHECK(xs, xe, 203)) {
+            mbar_arrive(bar);
+            return;
+        }
         mbar_arrive_expect_tx(bar, row_bytes);
         tma_load_1d(dst, src, row_bytes, bar);
     };
@@ -346,6 +360,9 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             const int px = lane, u = x0 + px, v = y0 + py, y = v + dyi - R;
             const bool rowok = decltype(interior)::value || ((u < W) && (v < H) && (y >= 0) && (y < H));
             const bool inner = decltype(interior)::value || (rowok && (u - R >= 0) && (u + R < W));
+            if (!SR_CHECK((py + dyi) * C::TXE + px + C::WS - 1, C::GUIDE, 204) ||
+                !SR_CHECK((py * C::WS + C::WS - 1) * kAggTX + px, C::WRING, 204))
+                continue;
             const float gc = guide[(py + R) * C::TXE + px + R];
             const float *grow = guide + (py + dyi) * C::TXE + px;
             const float fy = (float)((dyi - R) * (dyi - R)) * kd;
@@ -380,7 +397,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             const int r = i / C::TXE, c = i % C::TXE;
             const int y = y0 - R + r, x = x0 - R + c;
             g[k] = 0.0f;
-            if (i < C::GUIDE && y >= 0 && y < H && x >= 0 && x < W)
+            if (i < C::GUIDE && y >= 0 && y < H && x >= 0 && x < W && SR_CHECK(x, GU8 ? pitch : W, 205))
                 g[k] = GU8 ? (float)gl[(size_t)y * pitch + x] : gf[(size_t)y * W + x];
         }
 #pragma unroll
@@ -467,10 +484,23 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
                         // pair q: the diagonal elements at sh_off[q] (x)
                         // and sh_off[q + DL/2] (y)
 #pragma unroll
-                        for (int q = 0; q < DL / 2; ++q)
-                            cst[i][q] = make_float2(load_one(rs + sh_off[q] + i * C::CW),
-                                                    load_one(rs + sh_off[q + DL / 2] + i * C::CW));
-                    } else if constexpr (DL == 8) {
+                        for (int q = 0; q < DL / 2; ++q) {
+                            const int o = (bx + i) * C::CW;
+                            cst[i][q] = SR_CHECK(o + sh_off[q], C::RING, 206) &&
+                                                SR_CHECK(o + sh_off[q + DL / 2], C::RING, 206)
+                                            ? make_float2(load_one(rs + sh_off[q] + i * C::CW),
+                                                          load_one(rs + sh_off[q + DL / 2] + i * C::CW))
+                                            : make_float2(0.0f, 0.0f);
+                        }
+                        return;
+                    }
+                    // (checked builds: the column's last element lies in the slot)
+                    if (!SR_CHECK((bx + i) * C::CS + 4 * sl + (DL == 8 ? D / 2 : 0) + 3, C::RING, 206)) {
+#pragma unroll
+                        for (int q = 0; q < DL / 2; ++q) cst[i][q] = make_float2(0.0f, 0.0f);
+                        return;
+                    }
+                    if constexpr (DL == 8) {
                         // disparities 4 sl .. 4 sl + 3 and D/2 + 4 sl .. D/2 + 4 sl + 3
                         const float4 a = load_col4(rs + i * C::CS, sl);
                         const float4 b = load_col4(rs + i * C::CS + D / 2, sl);
@@ -495,7 +525,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
                             // the weights of the lane's pixels, each paired
                             // with itself for the paired multiply-add
                             float2 w[PX];
-                            if constexpr (PX == 2) {
+                            if (!SR_CHECK((py * C::WS + dx) * kAggTX + bx + PX - 1, C::WRING, 207)) {
+#pragma unroll
+                                for (int px = 0; px < PX; ++px) w[px] = make_float2(0.0f, 0.0f);
+                            } else if constexpr (PX == 2) {
                                 const float2 w2 = *reinterpret_cast<const float2 *>(
                                     ws + (py * C::WS + dx) * kAggTX);
                                 w[0] = make_float2(w2.x, w2.x);
@@ -549,6 +582,9 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
 #pragma unroll
         for (int px = 0; px < PX; ++px) {
             float *e = E + (grp * C::PPG + py * PX + px) * C::EPS;
+            if (!SR_CHECK((warp * C::PPG * C::G + grp * C::PPG + py * PX + px) * C::EPS + D - 1,
+                          kAggPix * C::EPS, 208))
+                continue;
             if constexpr (SH) {
 #pragma unroll
                 for (int q = 0; q < DL / 2; ++q) {
@@ -579,6 +615,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
         const int tpx = (warp * C::G + g) * PX + px;
         const int u = x0 + tpx, v = y0 + py;
         if (u >= W || v >= H) continue;
+        if (!SR_CHECK((warp * C::PPG * C::G + pw) * C::EPS + D - 1, kAggPix * C::EPS, 209)) continue;
         const float *e = E + pw * C::EPS;
         const size_t o = (size_t)v * W + u;
         // search window in slice indices: 0..D-1, or the pixel's window
@@ -632,7 +669,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             if (!WIN && win.post.disp) {   // Eq. 11 and Sec. II-C (see AggPost)
                 const int l = best + dlo, ur = u - l;
                 bool ok = false;
-                if (ur >= 0)
+                if (ur >= 0 && SR_CHECK(ur, W, 210))
                     ok = fabsf((float)(l - (int)win.post.lbl_r[(size_t)v * W + ur])) <=
                          win.post.lr_thresh;
                 win.post.disp[o] = ok ? post_disp(ds, win.post.rowsh[v]) : __int_as_float(0x7fc00000);
@@ -762,7 +799,9 @@ cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const floa
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
                                     dbg.wait_cycles, dbg.withhold_last, win, vpitch);
-    return cudaGetLastError();
+    cudaError_t el = cudaGetLastError();
+    SR_OOB_COLLECT(el, st);
+    return el;
 }
 
 template <int R, int D, typename VT>
@@ -777,7 +816,9 @@ cudaError_t agg_shear_launch_t(const CUtensorMap &tmap, int vpitch, const float 
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(tmap, vpitch, gf, W, H, kd, kr, lbl, agg, dbg.err,
                                     dbg.wait_cycles, dbg.withhold_last);
-    return cudaGetLastError();
+    cudaError_t el = cudaGetLastError();
+    SR_OOB_COLLECT(el, st);
+    return el;
 }
 
 template <int R, typename VT>
@@ -793,7 +834,9 @@ cudaError_t agg_band_launch_t(const CUtensorMap &tmap, const uint8_t *gl, int pi
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(tmap, gl, pitch, gf, W, H, kd, kr, lbl, dsub, dbg.err,
                                     dbg.wait_cycles, win);
-    return cudaGetLastError();
+    cudaError_t el = cudaGetLastError();
+    SR_OOB_COLLECT(el, st);
+    return el;
 }
 
 template <int R, int D, typename VT>
@@ -804,7 +847,9 @@ cudaError_t agg_batch_t(bool target, const PairDesc *pairs, const int *start, in
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     k<<<grid, C::NT, C::SMEM, st>>>(pairs, start, n, kd, kr, dbg.err, dbg.wait_cycles, next);
-    return cudaGetLastError();
+    cudaError_t el = cudaGetLastError();
+    SR_OOB_COLLECT(el, st);
+    return el;
 }
 
 template <int R, int D, typename VT>

@@ -93,8 +93,10 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     const bool inside = u < Wo && v < H;
     const size_t rowo = (size_t)(inside ? v : 0) * WE;
     const int uc = inside ? u : 0;
-    const float m = TARGET ? mu_r[rowo + uc + D - 1] : mu_l[rowo + uc];
-    const float inv_f0 = TARGET ? inv_r[rowo + uc + D - 1] : inv_l[rowo + uc];
+    const size_t fo = rowo + uc + (TARGET ? D - 1 : 0);   // statistics rows are H x WE
+    const bool fok = SR_CHECK(fo, (long long)H * WE, 101);
+    const float m = !fok ? 0.0f : TARGET ? mu_r[fo] : mu_l[fo];
+    const float inv_f0 = !fok ? 0.0f : TARGET ? inv_r[fo] : inv_l[fo];
 
     // Stage the fixed and sliding tiles (clamp-to-edge).
     const int fx0 = x0 - RN;
@@ -102,11 +104,13 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
     for (int i = tid; i < TH * FW; i += kNccThreads) {
         const int r = i / FW, c = i % FW;
         const int y = clampi(y0 - RN + r, 0, H - 1), x = clampi(fx0 + c, 0, W - 1);
+        if (!SR_CHECK(x, TARGET ? W : pitch, 102) || !SR_CHECK(y, H, 102)) continue;
         sm.fix_s[r][c] = TARGET ? rw[(size_t)y * W + x] : (float)left[(size_t)y * pitch + x];
     }
     for (int i = tid; i < TH * SW; i += kNccThreads) {
         const int r = i / SW, c = i % SW;
         const int y = clampi(y0 - RN + r, 0, H - 1), x = clampi(sx0 + c, 0, W - 1);
+        if (!SR_CHECK(x, TARGET ? pitch : W, 103) || !SR_CHECK(y, H, 103)) continue;
         const float val = TARGET ? (float)left[(size_t)y * pitch + x] : rw[(size_t)y * W + x];
         sm.sld_s[r][c] = val - kNccOffset;
     }
@@ -120,6 +124,7 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
             const int r = i / XW, t = i % XW;
             const int y = clampi(y0 + r, 0, H - 1);
             const int xi = clampi(x0 + t, 0, WE - 1);
+            if (!SR_CHECK((size_t)y * WE + xi, (long long)H * WE, 104)) continue;
             sm.sst_s[r][t] = make_float2(mu_s[(size_t)y * WE + xi] - kNccOffset,
                                          inv_s[(size_t)y * WE + xi]);
         }
@@ -163,7 +168,8 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
             const int sc = TARGET ? tx + k + RN : tx - k + RN + D - 1;
             float col[B];
 #pragma unroll
-            for (int oy = 0; oy < B; ++oy) col[oy] = sm.sld_s[ty + oy][sc];
+            for (int oy = 0; oy < B; ++oy)
+                col[oy] = SR_CHECK(sc, SW, 105) && SR_CHECK(ty + oy, TH, 105) ? sm.sld_s[ty + oy][sc] : 0.0f;
 #pragma unroll
             for (int ox = 0; ox < B; ++ox) {
                 const int dl = TARGET ? kk - ox : kk + ox - 2 * RN;   // d - d0
@@ -180,7 +186,8 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
 #pragma unroll
         for (int i = 0; i < DC; ++i) {
             const int so = TARGET ? d0 + i : -(d0 + i);
-            const float2 ss = st_s_row[so];
+            const float2 ss = SR_CHECK((TARGET ? tx : tx + D - 1) + so, XW, 106) ? st_s_row[so]
+                                                                                 : make_float2(0.0f, 0.0f);
             const float num = fmaf(-sa, ss.x, acc[i]);
             cst[i] = num * inv_f * ss.y;
             // extended volume: a sliding centre u - d >= W has no statistics
@@ -189,7 +196,9 @@ __device__ __forceinline__ void ncc_tile(NccSmem<RN, D> &sm, const uint8_t *__re
             if (!TARGET && u - (d0 + i) >= W) cst[i] = 0.0f;
         }
 #pragma unroll
-        for (int i = 0; i < DC; i += 8) store8(out + d0 + i, cst + i);
+        for (int i = 0; i < DC; i += 8)
+            if (SR_CHECK(((size_t)v * Wo + u) * D + d0 + i + 7, (long long)H * Wo * D, 107))
+                store8(out + d0 + i, cst + i);
     }
 }
 
@@ -249,7 +258,9 @@ cudaError_t ncc_launch_t(bool target, const uint8_t *left, int pitch, const floa
         k_ncc<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, Wo, range);
     else
         k_ncc<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, vol, Wo, range);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 template <int RN, int D, typename VT>
@@ -259,7 +270,9 @@ cudaError_t ncc_batch_t(bool target, const PairDesc *pairs, const int *start, in
         k_ncc_batch<RN, D, true, VT><<<grid, kNccThreads, 0, st>>>(pairs, start, n, next);
     else
         k_ncc_batch<RN, D, false, VT><<<grid, kNccThreads, 0, st>>>(pairs, start, n, next);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 template <int RN, int D, typename VT>

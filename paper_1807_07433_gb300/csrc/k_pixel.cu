@@ -123,7 +123,7 @@ __device__ __forceinline__ void lrc_px(const int16_t *__restrict__ lbl_l,
     const int l = lbl_l[i];
     const int ur = u - l;
     bool ok = false;
-    if (ur >= 0) ok = fabsf((float)(l - (int)lbl_r[(size_t)v * W + ur])) <= lr_thresh;
+    if (ur >= 0 && SR_CHECK(ur, W, 301)) ok = fabsf((float)(l - (int)lbl_r[(size_t)v * W + ur])) <= lr_thresh;
     disp[i] = ok ? post_disp(dsub[i], sh) : __int_as_float(0x7fc00000);
     if (wta_out) wta_out[i] = (int16_t)l;
 }
@@ -211,9 +211,10 @@ __global__ void k_lrc_post_batch(const PairDesc *__restrict__ pairs, const int *
 }
 
 __global__ void k_xyz(const float *__restrict__ disp, int W, int H, float f, float fb, float u0,
-                      float v0, float *__restrict__ xyz) {
+                      float v0, float *__restrict__ xyz, int selftest) {
     const int u = blockIdx.x * kBX + threadIdx.x;
     const int v = blockIdx.y * kBY + threadIdx.y;
+    if (selftest && u == 0 && v == 0) (void)SR_CHECK(-1, 1, 399);   // no access follows
     if (u >= W || v >= H) return;
     const size_t i = (size_t)v * W + u, npx = (size_t)W * H;
     const float d = disp[i];
@@ -263,7 +264,8 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     if (tid < TH) {
         const int y = clampi(y0 - RN + tid, 0, H - 1);
         const double sh = row_shift(alpha0, alpha1, delta, y + row0);
-        if (blockIdx.x == 0 && tid >= RN && tid < RN + kBY && y0 - RN + tid < H)
+        if (blockIdx.x == 0 && tid >= RN && tid < RN + kBY && y0 - RN + tid < H &&
+            SR_CHECK(y0 - RN + tid, H, 302))
             rowsh[y0 - RN + tid] = split_shift(sh);   // one column of tiles writes each row
         double k = floor(sh);
         s_w[tid] = (float)(sh - k);
@@ -280,11 +282,15 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
             const int i = min(tid + k * kBX * kBY, TH * TW - 1);
             const int r = i / TW, c = i % TW;
             const int y = clampi(y0 - RN + r, 0, H - 1);
-            lv[k] = left[(size_t)y * pitch + clampi(x0 - RN + c, 0, W - 1)];
+            const int xl = clampi(x0 - RN + c, 0, W - 1);
             const int x = clampi(xr0 - RN + c, 0, W - 1);
+            const int xa = clampi(x - s_k[r], 0, W - 1), xb = clampi(x - s_k[r] - 1, 0, W - 1);
             const uint8_t *row = right + (size_t)y * pitch;
-            av[k] = row[clampi(x - s_k[r], 0, W - 1)];
-            bv[k] = row[clampi(x - s_k[r] - 1, 0, W - 1)];
+            const bool okl = SR_CHECK(xl, pitch, 303) && SR_CHECK(y, H, 303);
+            const bool okr = SR_CHECK(xa, pitch, 304) && SR_CHECK(xb, pitch, 304);
+            lv[k] = okl ? left[(size_t)y * pitch + xl] : 0;
+            av[k] = okr && okl ? row[xa] : 0.0f;
+            bv[k] = okr && okl ? row[xb] : 0.0f;
         }
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
@@ -313,6 +319,7 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int xi = x0 + tx, v = y0 + ty;
     if (xi >= WE || v >= H) return;
+    if (!SR_CHECK((size_t)v * WE + xi, (long long)H * WE, 305)) return;
     // left block at centre xi (exact integer sums)
     {
         unsigned su = 0, s2 = 0;
@@ -351,7 +358,7 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     }
     // the warped image, at the target columns this tile owns
     const int xr = xi - (D - 1);
-    if (xr >= 0) rw[(size_t)v * W + xr] = s_r[ty + RN][tx + RN];
+    if (xr >= 0 && SR_CHECK(xr, W, 306)) rw[(size_t)v * W + xr] = s_r[ty + RN][tx + RN];
 }
 
 }  // namespace
@@ -371,13 +378,17 @@ cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, in
 #undef SR_PREP
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 cudaError_t launch_warp(const uint8_t *right, int pitch, int W, int H, double alpha0,
                         double alpha1, double delta, float *rw, cudaStream_t st) {
     k_warp<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(right, pitch, W, H, alpha0, alpha1, delta, rw);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 template <int RN>
@@ -399,7 +410,9 @@ cudaError_t launch_stats(const uint8_t *left, int pitch, const float *rw, int W,
         case 5: stats_rn<5>(left, pitch, rw, W, H, D, mu_l, inv_l, mu_r, inv_r, st); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const float *dsub, int W,
@@ -407,13 +420,17 @@ cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const fl
                             int16_t *wta_out, cudaStream_t st) {
     k_lrc_post<<<grid_for(ceil_div(W, kLrcPX), H), dim3(kBX, kBY), 0, st>>>(
         lbl_l, lbl_r, dsub, W, H, rowsh, lr_thresh, disp, wta_out);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 cudaError_t launch_warp_batch(const PairDesc *pairs, const int *start, int n, int grid,
                               cudaStream_t st) {
     k_warp_batch<<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 cudaError_t launch_stats_batch(const PairDesc *pairs, const int *start, int n, int D, int ncc_r,
@@ -426,21 +443,27 @@ cudaError_t launch_stats_batch(const PairDesc *pairs, const int *start, int n, i
         case 5: k_stats_batch<5><<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, D); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 cudaError_t launch_lrc_post_batch(const PairDesc *pairs, const int *start, int n, float lr_thresh,
                                   int grid, cudaStream_t st) {
     k_lrc_post_batch<<<grid, dim3(kBX, kBY), 0, st>>>(pairs, start, n, lr_thresh);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 cudaError_t launch_xyz(const float *disp, int W, int H, double f_px, double baseline, double u0,
-                       double v0, float *xyz, cudaStream_t st) {
+                       double v0, float *xyz, cudaStream_t st, bool selftest) {
     k_xyz<<<grid_for(W, H), dim3(kBX, kBY), 0, st>>>(disp, W, H, (float)f_px,
                                                     (float)(f_px * baseline), (float)u0,
-                                                    (float)v0, xyz);
-    return cudaGetLastError();
+                                                    (float)v0, xyz, selftest ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    SR_OOB_COLLECT(e, st);
+    return e;
 }
 
 }  // namespace sr

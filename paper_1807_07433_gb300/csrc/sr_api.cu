@@ -378,6 +378,7 @@ const char *sr_status_str(sr_status s) {
         case SR_ERR_CUDA: return "SR_ERR_CUDA";
         case SR_ERR_STATE: return "SR_ERR_STATE";
         case SR_ERR_TIMEOUT: return "SR_ERR_TIMEOUT";
+        case SR_ERR_BOUNDS: return "SR_ERR_BOUNDS";
     }
     return "SR_ERR_UNKNOWN";
 }
@@ -471,7 +472,8 @@ sr_status sr_set_camera(sr_ctx *c, double f_px, double baseline, double u0, doub
 }
 
 sr_status sr_set_debug(sr_ctx *c, int flags) {
-    if (!c || (flags & ~(SR_DEBUG_KEEP_AGG | SR_DEBUG_WITHHOLD_ROW | SR_DEBUG_NO_BAND)))
+    if (!c || (flags & ~(SR_DEBUG_KEEP_AGG | SR_DEBUG_WITHHOLD_ROW | SR_DEBUG_NO_BAND |
+                   SR_DEBUG_BOUNDS_SELFTEST)))
         return SR_ERR_INVALID_ARG;
     if ((flags & SR_DEBUG_KEEP_AGG) && !c->agg_l) {
         const size_t n = (size_t)c->p.width * c->p.height * c->p.max_disp;
@@ -838,7 +840,7 @@ sr_status sr_reconstruct(sr_ctx *c, const float *d_disp, float *d_xyz) {
     if (!c || !d_disp || !d_xyz) return SR_ERR_INVALID_ARG;
     if (!c->camera) return SR_ERR_STATE;
     SR_TRY(c, sr::launch_xyz(d_disp, c->p.width, c->p.height, c->f_px, c->baseline, c->u0, c->v0,
-                             d_xyz, c->st),
+                             d_xyz, c->st, (c->debug & SR_DEBUG_BOUNDS_SELFTEST) != 0),
            "xyz");
     return SR_OK;
 }
@@ -1073,3 +1075,50 @@ sr_status sr_get_buffer(sr_ctx *c, sr_buffer which, void *dst, size_t *bytes_ino
 }
 
 }  // extern "C"
+
+// ---- bounds-checked build: host record of offences (see sr_internal.cuh) ----
+#ifdef SR_BOUNDS_CHECK
+#include <mutex>
+namespace sr {
+namespace {
+std::mutex g_oob_mu;
+unsigned long long g_oob_word = 0;   // first offence since the last report
+long long g_oob_count = 0;
+char g_oob_unit[160] = {0};
+}  // namespace
+void oob_record(unsigned long long word, const char *unit) {
+    std::lock_guard<std::mutex> lk(g_oob_mu);
+    if (g_oob_word == 0) {
+        g_oob_word = word;
+        snprintf(g_oob_unit, sizeof(g_oob_unit), "%s", unit ? unit : "");
+    }
+    ++g_oob_count;
+    SR_LOG(1, "bounds check: site %d, index %lld (%s)", (int)((word >> 48) & 0x7fff),
+           (long long)(word & 0xffffffffffffull), unit ? unit : "");
+}
+}  // namespace sr
+#endif
+
+extern "C" sr_status sr_bounds_report(int *site, long long *index, char *unit, int unit_len,
+                                      long long *count) {
+#ifndef SR_BOUNDS_CHECK
+    (void)site; (void)index; (void)unit; (void)unit_len; (void)count;
+    return SR_ERR_UNSUPPORTED;
+#else
+    std::lock_guard<std::mutex> lk(sr::g_oob_mu);
+    const unsigned long long w = sr::g_oob_word;
+    if (site) *site = w ? (int)((w >> 48) & 0x7fff) : -1;
+    if (index) {
+        // the 48-bit index field, sign-extended
+        long long i = (long long)(w & 0xffffffffffffull);
+        if (i & (1ll << 47)) i -= (1ll << 48);
+        *index = w ? i : 0;
+    }
+    if (unit && unit_len > 0) snprintf(unit, (size_t)unit_len, "%s", w ? sr::g_oob_unit : "");
+    if (count) *count = sr::g_oob_count;
+    sr::g_oob_word = 0;
+    sr::g_oob_count = 0;
+    sr::g_oob_unit[0] = 0;
+    return w ? SR_ERR_BOUNDS : SR_OK;
+#endif
+}

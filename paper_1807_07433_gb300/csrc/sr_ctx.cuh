@@ -111,6 +111,11 @@ struct NvtxRange {
 };
 
 inline sr_status fail_cuda(sr_ctx *c, cudaError_t e, const char *what) {
+    if (e == sr::kOobError) {   // only a bounds-checked build's launchers return it
+        if (c) snprintf(c->err, sizeof(c->err), "%s: an index outside its buffer (sr_bounds_report)", what);
+        SR_LOG(1, "%s: an index outside its buffer", what);
+        return SR_ERR_BOUNDS;
+    }
     if (c) snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
     SR_LOG(1, "%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;

@@ -8,6 +8,55 @@
 
 namespace sr {
 
+// ---- bounds-checked build (-DSR_BOUNDS_CHECK) ------------------------------
+// SR_CHECK(i, n, site) is true when 0 <= i < n.  Otherwise it records the
+// first offender of this translation unit -- site number and index -- in the
+// device word g_sr_oob and is false, and the caller skips the access (a
+// skipped load reads 0).  After each launch the unit's launcher calls
+// SR_OOB_COLLECT, which (outside stream capture) synchronises the stream,
+// moves a recorded offence to the host record (oob_record, sr_api.cu) and
+// returns kOobError, which the C ABI reports as SR_ERR_BOUNDS.  In release
+// builds SR_CHECK is the constant true and SR_OOB_COLLECT does nothing.
+// Site numbers: 1xx NCC, 2xx aggregation, 3xx per-pixel kernels.
+constexpr cudaError_t kOobError = cudaErrorAssert;   // no kernel here asserts
+#ifdef SR_BOUNDS_CHECK
+static __device__ unsigned long long g_sr_oob;
+__device__ __forceinline__ bool sr_check(long long i, long long n, int site) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&g_sr_oob, 0ull,
+              (1ull << 63) | ((unsigned long long)(site & 0x7fff) << 48) |
+                  ((unsigned long long)i & 0xffffffffffffull));
+    return false;
+}
+// host record of an offence (the word above, the unit's source file)
+void oob_record(unsigned long long word, const char *unit);
+static inline cudaError_t sr_oob_collect(cudaStream_t st, const char *unit) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return cudaSuccess;   // a captured launch is checked by the next plain one
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    unsigned long long w = 0;
+    e = cudaMemcpyFromSymbol(&w, g_sr_oob, sizeof(w));
+    if (e != cudaSuccess) return e;
+    if (!w) return cudaSuccess;
+    oob_record(w, unit);
+    const unsigned long long z = 0;
+    e = cudaMemcpyToSymbol(g_sr_oob, &z, sizeof(z));
+    return e != cudaSuccess ? e : kOobError;
+}
+#define SR_CHECK(i, n, site) ::sr::sr_check((long long)(i), (long long)(n), (site))
+#define SR_OOB_COLLECT(e, st)                                                   \
+    do {                                                                        \
+        if ((e) == cudaSuccess) (e) = ::sr::sr_oob_collect((st), __BASE_FILE__); \
+    } while (0)
+#else
+#define SR_CHECK(i, n, site) true
+#define SR_OOB_COLLECT(e, st) \
+    do {                      \
+    } while (0)
+#endif
+
 // Offset subtracted from the sliding block in the NCC dot product.  Any
 // constant leaves Eq. 3 unchanged (the fixed block is centred, so the sum of
 // its centred values is zero); 128 keeps the products small for 0..255 data.
@@ -205,8 +254,10 @@ cudaError_t launch_lrc_post(const int16_t *lbl_l, const int16_t *lbl_r, const fl
                             int16_t *wta_out, cudaStream_t st);
 
 // Sec. II-D reconstruction, three planes X, Y, Z of [H][W].
+// selftest (bounds-checked builds): one thread evaluates a failing check
+// (site 399) with no memory access.
 cudaError_t launch_xyz(const float *disp, int W, int H, double f_px, double baseline, double u0,
-                       double v0, float *xyz, cudaStream_t st);
+                       double v0, float *xyz, cudaStream_t st, bool selftest = false);
 
 // Adjoint of L = sum_{dstar >= 0} c_agg(p, dstar[p]) (Eq. 8 over Eq. 3 on the
 // Sec. II-A warp) with respect to alpha and the images; rw, the block

@@ -15,20 +15,23 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsr.so")
+CHECK_LIB_PATH = os.path.join(_HERE, "libsr_check.so")   # bounds-checked build
 
 SR_OK, SR_ERR_INVALID_ARG, SR_ERR_UNSUPPORTED, SR_ERR_OOM, SR_ERR_CUDA, SR_ERR_STATE, \
-    SR_ERR_TIMEOUT = range(7)
+    SR_ERR_TIMEOUT, SR_ERR_BOUNDS = range(8)
 SR_VOL_F32, SR_VOL_F16, SR_VOL_BF16 = range(3)
 (SR_BUF_WARPED, SR_BUF_MU_L, SR_BUF_INV_L, SR_BUF_MU_R, SR_BUF_INV_R, SR_BUF_COST_L,
  SR_BUF_COST_R, SR_BUF_AGG_L, SR_BUF_AGG_R, SR_BUF_WTA_L, SR_BUF_WTA_R, SR_BUF_DSUB) = range(12)
 SR_DEBUG_KEEP_AGG = 1
 SR_DEBUG_WITHHOLD_ROW = 2
 SR_DEBUG_NO_BAND = 4
+SR_DEBUG_BOUNDS_SELFTEST = 8
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
            "sr_match_restricted", "sr_match_rows",
            "sr_match_host", "sr_match_host_async", "sr_match_noalloc", "sr_noalloc_status",
+           "sr_bounds_report",
            "sr_match_batch", "sr_set_autotune",
            "sr_set_batch_schedule", "sr_batch_info", "sr_reconstruct", "sr_grad_plane",
            "sr_fit_alpha", "sr_fit_roll",
@@ -90,6 +93,8 @@ def load(path: str | None = None):
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
                 "sr_noalloc_status": (i, [vp]),
+                "sr_bounds_report": (i, [ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong)]),
                 "sr_match_batch": (i, [vp, i, ctypes.POINTER(sr_pair_desc)]),
                 "sr_set_autotune": (i, [vp, i, ctypes.c_char_p]),
                 "sr_batch_info": (i, [vp, ctypes.c_char_p, sz]),
@@ -223,6 +228,17 @@ def sr_noalloc_status(cuda_stream=None) -> None:
     of an sr_match_noalloc call in the current context ran out since the last
     check (the condition is then cleared)."""
     _check(None, load().sr_noalloc_status(_stream_handle(cuda_stream)), "sr_noalloc_status")
+
+
+def sr_bounds_report():
+    """Bounds-checked build: (status, site, index, unit, count) of the first
+    out-of-range index recorded since the last report (status SR_OK: none,
+    SR_ERR_BOUNDS: one; SR_ERR_UNSUPPORTED in a release build); clears it."""
+    site, index, count = ctypes.c_int(-1), ctypes.c_longlong(0), ctypes.c_longlong(0)
+    unit = ctypes.create_string_buffer(160)
+    st = load().sr_bounds_report(ctypes.byref(site), ctypes.byref(index), unit, 160,
+                                 ctypes.byref(count))
+    return st, site.value, index.value, unit.value.decode(errors="replace"), count.value
 
 
 def make_pair_desc(left, right, disp, alpha0, alpha1, delta, wta=None) -> sr_pair_desc:
