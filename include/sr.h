@@ -285,9 +285,15 @@ typedef struct {
  * whole batch; sr_set_batch_schedule and sr_set_autotune select among
  * other schedules.  The context supplies D, the radii, gamma_d, gamma_r,
  * lr_thresh, vol_dtype and the stream; its width and height are not used.
- * Scratch for the whole batch (about sum of ((2*W + D)*H*D*e + 40*W*H) bytes, e as
- * for sr_create) is allocated on first use and grown when a larger batch
- * arrives.  Results are identical to n sr_match calls.  Asynchronous.
+ * Scratch is held by the context and sized for the schedule that runs:
+ * the per-pair schedules (4-7) run the pairs of one stream in order and give
+ * each stream one slot sized for its largest pair (schedules 6-7: about
+ * (W + D)*H*D*e + 40*W*H bytes, e as for sr_create; 4-5 add W*H*D*e for the
+ * target volume), so scratch is bounded by the streams, not by n; the
+ * persistent schedules (0-3) run all pairs at once and need one slot per
+ * pair.  The autotuner skips a schedule whose scratch would not fit the free
+ * device memory, and after its choice the pool shrinks to that schedule's
+ * need.  Results are identical to n sr_match calls.  Asynchronous.
  * Errors: SR_ERR_INVALID_ARG (n < 1, a bad pair), SR_ERR_OOM, SR_ERR_CUDA. */
 sr_status sr_match_batch(sr_ctx *ctx, int n, const sr_pair_desc *pairs);
 

@@ -72,6 +72,8 @@ struct SrBatch {
     bool staged_pending = false;
     void *pool = nullptr;
     size_t pool_bytes = 0;
+    bool tuning = false;                      // inside the autotuner's loop
+    bool shrink_next = false;                 // the tuner chose: fit the pool to it
     cudaStream_t cap_stream = nullptr;        // capture stream (never the legacy one)
     cudaStream_t side[kMaxSide] = {};         // forked capture streams (schedule B)
     cudaEvent_t fork = nullptr, join[kMaxSide] = {};
@@ -114,14 +116,54 @@ void sr_batch_free(sr_ctx *c) {
 
 namespace {
 
-// Per-pair scratch (same arrays sr_create allocates for one frame).
-size_t pair_scratch_bytes(const sr_params &p, int W, int H) {
+// Scratch of one pair (the arrays sr_create allocates for one frame).
+// vol_l holds the extended reference volume [H][WE][D] (schedule C) or the
+// reference volume [H][W][D] (the other schedules, a prefix of it); the
+// target volume vol_r is needed by all schedules but C, which reads both
+// views from vol_l.
+size_t pair_scratch_bytes(const sr_params &p, int W, int H, bool with_vol_r) {
     const size_t npx = (size_t)W * H, WE = (size_t)W + p.max_disp - 1;
     const size_t e = sr::vol_elem_bytes(p.vol_dtype);
-    // vol_l holds the extended reference volume [H][WE][D] (schedule C) or the
-    // reference volume [H][W][D] (persistent schedules, a prefix of it)
     return 2 * a256(npx * 4) + 4 * a256((size_t)H * WE * 4) + a256((size_t)H * WE * p.max_disp * e) +
-           a256(npx * p.max_disp * e) + 2 * a256(npx * 2) + a256((size_t)H * 8);
+           (with_vol_r ? a256(npx * p.max_disp * e) : 0) + 2 * a256(npx * 2) + a256((size_t)H * 8);
+}
+
+// Scratch slots of a schedule: the per-pair schedules run the pairs of one
+// stream in order (pair k on stream k mod S), so the pairs of a stream share
+// one slot sized for the largest of them; the persistent schedules run all
+// pairs at once, one slot each.  Fills slot_of (per staged pair) and returns
+// the pool bytes.
+size_t slot_layout(const sr_params &p, int n, const sr_pair_desc *pairs, const int *order,
+                   int variant, std::vector<size_t> *slot_off, std::vector<int> *slot_of) {
+    const bool pp = per_pair(variant);
+    const int S = pp ? pair_streams(variant) : n;
+    std::vector<size_t> bytes(S, 0);
+    slot_of->resize(n);
+    for (int k = 0; k < n; ++k) {
+        const int s = pp ? k % S : k;
+        (*slot_of)[k] = s;
+        const sr_pair_desc &q = pairs[order[k]];
+        bytes[s] = std::max(bytes[s], pair_scratch_bytes(p, q.width, q.height, !sched_c(variant)));
+    }
+    slot_off->assign(S, 0);
+    size_t total = 0;
+    for (int s = 0; s < S; ++s) {
+        (*slot_off)[s] = total;
+        total += bytes[s];
+    }
+    return total;
+}
+
+// Order of the staged pairs: caller order, or largest first.
+std::vector<int> stage_order(int n, const sr_pair_desc *pairs, int variant) {
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    if ((variant & 2) || per_pair(variant))
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
+            return (long long)pairs[a].width * pairs[a].height >
+                   (long long)pairs[b2].width * pairs[b2].height;
+        });
+    return order;
 }
 
 std::string tune_key(const sr_ctx *c, int n, const sr_pair_desc *pairs) {
@@ -290,18 +332,28 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
                         cudaStream_t st) {
     const sr_params &p = c->p;
     const int D = p.max_disp;
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    if ((variant & 2) || per_pair(variant))
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
-            return (long long)pairs[a].width * pairs[a].height >
-                   (long long)pairs[b2].width * pairs[b2].height;
-        });
+    const std::vector<int> order = stage_order(n, pairs, variant);
     if (b->staged_pending) {
         cudaError_t e = cudaEventSynchronize(b->staged);   // staging buffers free again
         if (e != cudaSuccess) return e;
     }
-    unsigned char *q = static_cast<unsigned char *>(b->pool);
+    std::vector<size_t> slot_off;
+    std::vector<int> slot_of;
+    const size_t need = slot_layout(p, n, pairs, order.data(), variant, &slot_off, &slot_of);
+    // grow the pool; shrink it to the schedule's need right after the
+    // tuner's choice, and otherwise when it holds more than twice the need
+    const bool shrink = !b->tuning && (b->shrink_next ? need < b->pool_bytes : need < b->pool_bytes / 2);
+    if (!b->tuning) b->shrink_next = false;
+    if (need > b->pool_bytes || shrink) {
+        cudaError_t e = cudaStreamSynchronize(st);   // no launch still reads the pool
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) return e;
+        if (b->pool) cudaFree(b->pool);
+        b->pool = nullptr;
+        b->pool_bytes = 0;
+        if ((e = cudaMalloc(&b->pool, need)) != cudaSuccess) return e;
+        b->pool_bytes = need;
+    }
     int *sp = b->h_start, *ss = b->h_start + (b->cap + 1), *s4 = b->h_start + 2 * (b->cap + 1);
     int *per = b->h_start + kBatchStages * (b->cap + 1);
     sp[0] = ss[0] = s4[0] = 0;
@@ -318,6 +370,7 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
         o.left = in.d_left; o.right = in.d_right;
         o.alpha0 = in.alpha0; o.alpha1 = in.alpha1; o.delta = in.delta;
         o.disp = in.d_disp; o.wta = in.d_wta_or_null;
+        unsigned char *q = static_cast<unsigned char *>(b->pool) + slot_off[slot_of[k]];
         auto take = [&q](size_t bytes) { unsigned char *r = q; q += a256(bytes); return r; };
         o.rw = reinterpret_cast<float *>(take(npx * 4));
         o.dsub = reinterpret_cast<float *>(take(npx * 4));
@@ -326,7 +379,7 @@ cudaError_t stage_batch(sr_ctx *c, SrBatch *b, int n, const sr_pair_desc *pairs,
         o.mu_r = reinterpret_cast<float *>(take((size_t)H * WE * 4));
         o.inv_r = reinterpret_cast<float *>(take((size_t)H * WE * 4));
         o.vol_l = take((size_t)H * WE * D * sr::vol_elem_bytes(p.vol_dtype));
-        o.vol_r = take(npx * D * sr::vol_elem_bytes(p.vol_dtype));
+        o.vol_r = sched_c(variant) ? nullptr : take(npx * D * sr::vol_elem_bytes(p.vol_dtype));
         o.lbl_l = reinterpret_cast<int16_t *>(take(npx * 2));
         o.lbl_r = reinterpret_cast<int16_t *>(take(npx * 2));
         o.rowsh = reinterpret_cast<float2 *>(take((size_t)H * 8));
@@ -448,18 +501,9 @@ sr_status sr_match_batch(sr_ctx *c, int n, const sr_pair_desc *pairs) {
     if (!b->sms) SR_TRY(c, cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, c->device), "attr");
     if (!b->d_next) SR_TRY(c, cudaMalloc(&b->d_next, 4 * sizeof(int)), "cudaMalloc(counters)");
     SR_TRY(c, ensure_capacity(b, n), "batch descriptors");
-    size_t need = 0;
-    for (int i = 0; i < n; ++i) need += pair_scratch_bytes(c->p, pairs[i].width, pairs[i].height);
-    if (need > b->pool_bytes) {
-        if (b->staged_pending) cudaEventSynchronize(b->staged);
-        SR_TRY(c, cudaStreamSynchronize(c->st), "cudaStreamSynchronize");
-        if (b->pool) cudaFree(b->pool);
-        b->pool = nullptr;
-        b->pool_bytes = 0;
-        SR_TRY(c, cudaMalloc(&b->pool, need), "cudaMalloc(batch scratch)");
-        b->pool_bytes = need;
-    }
+    // (the scratch pool is sized by stage_batch for the schedule it stages)
 
+    b->tuning = false;
     int variant = 0;
     if (b->forced >= 0) {
         variant = b->forced;
@@ -474,7 +518,20 @@ sr_status sr_match_batch(sr_ctx *c, int n, const sr_pair_desc *pairs) {
             SR_TRY(c, cudaEventCreate(&e0), "event");
             SR_TRY(c, cudaEventCreate(&e1), "event");
             float best = 1e30f;
+            b->tuning = true;   // the pool keeps the largest layout until the choice
             for (int v = 0; v < kVariants; ++v) {
+                // a schedule whose scratch would not fit the free memory
+                // (keeping 1 GiB) is not timed: tune_ms -1
+                std::vector<size_t> so;
+                std::vector<int> sl;
+                const std::vector<int> ord = stage_order(n, pairs, v);
+                const size_t need = slot_layout(c->p, n, pairs, ord.data(), v, &so, &sl);
+                size_t free_b = 0, total_b = 0;
+                cudaMemGetInfo(&free_b, &total_b);
+                if (need > b->pool_bytes && need - b->pool_bytes + (size_t(1) << 30) > free_b) {
+                    b->tune_ms[v] = -1.0f;
+                    continue;
+                }
                 float t_best = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
                     SR_TRY(c, stage_batch(c, b, n, pairs, v, c->st), "stage");
@@ -489,6 +546,8 @@ sr_status sr_match_batch(sr_ctx *c, int n, const sr_pair_desc *pairs) {
                 b->tune_ms[v] = t_best;
                 if (t_best < best) { best = t_best; variant = v; }
             }
+            b->tuning = false;
+            b->shrink_next = true;
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             b->tuned[key] = variant;

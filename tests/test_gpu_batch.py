@@ -220,6 +220,37 @@ def test_batch_at_the_mixed_workload_sizes(vt):
         sr.sr_set_autotune(m.ctx, True)
         _same(_batch(m.ctx, pairs), want)
         _same(_batch(m.ctx, pairs, order=[3, 1, 0, 2]), want)
+        info = sr.sr_batch_info(m.ctx)
+        if info["variant"] >= 6:
+            # one slot per stream, each at most the largest pair's arrays
+            e = 4 if vt == sr.SR_VOL_F32 else 2
+            W, H = 2208, 1242
+            slot = 2 * W * H * 4 + 4 * H * (W + 63) * 4 + H * (W + 63) * 64 * e + 2 * W * H * 2 + H * 8
+            streams = min(info["streams"], len(pairs))
+            assert info["scratch_bytes"] <= streams * (slot + 16 * 256), info
+
+
+def test_scratch_is_bounded_by_streams_not_pairs():
+    """Twelve small pairs under the 4-stream schedule of sr_match's kernels
+    (7) take four slots of scratch; the persistent schedule (0) one per pair;
+    the results are the same."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    pairs = []
+    for k in range(12):
+        sc = synth.Scene(96 + 8 * (k % 3), 40, 12.0, 0.05, 1, False, 2000 + k)
+        left, right, _ = synth.make_pair(sc)
+        pairs.append((left, right, sc.alpha0, sc.alpha1, 8.0))
+    with sr.Matcher(8, 8, 64, 2, 3, 3.0, 10.0, stream=torch.cuda.current_stream()) as m:
+        sr.sr_set_batch_schedule(m.ctx, 0)
+        out0 = _batch(m.ctx, pairs)
+        s0 = sr.sr_batch_info(m.ctx)["scratch_bytes"]
+        sr.sr_set_batch_schedule(m.ctx, 7)
+        out7 = _batch(m.ctx, pairs)
+        s7 = sr.sr_batch_info(m.ctx)["scratch_bytes"]
+    _same(out7, out0)
+    # four slots of the largest pair (widths 96..112) against twelve slots
+    assert s7 <= 4 * (s0 / 12) * 1.2, (s7, s0)
 
 
 def test_autotune_cache_path_from_environment(tmp_path, monkeypatch):
