@@ -266,6 +266,7 @@ void free_all(sr_ctx *c) {
     }
     if (c->up) cudaStreamDestroy(c->up);
     if (c->down) cudaStreamDestroy(c->down);
+    if (c->h_err_async) cudaFreeHost(c->h_err_async);
     sr_batch_free(c);
 }
 
@@ -800,6 +801,8 @@ sr_status sr_match_host_async(sr_ctx *c, const uint8_t *h_left, const uint8_t *h
     if (!c->up) {
         SR_TRY(c, cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking), "cudaStreamCreate");
         SR_TRY(c, cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking), "cudaStreamCreate");
+        SR_TRY(c, cudaMallocHost(&c->h_err_async, 2 * sizeof(int)), "cudaMallocHost(err)");
+        c->h_err_async[0] = c->h_err_async[1] = 0;
         for (int i = 0; i < 2; ++i) {
             SR_TRY(c, cudaEventCreateWithFlags(&c->ev_up[i], cudaEventDisableTiming), "cudaEventCreate");
             SR_TRY(c, cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming), "cudaEventCreate");
@@ -813,8 +816,16 @@ sr_status sr_match_host_async(sr_ctx *c, const uint8_t *h_left, const uint8_t *h
         // the frame queued two calls ago used this slot: let it finish, so
         // that its result is in its host buffer and its inputs are free
         SR_TRY(c, cudaEventSynchronize(c->ev_down[k]), "cudaEventSynchronize");
-        sr_status s = take_device_error(c);
-        if (s != SR_OK) return s;
+        // the error word as that frame's download left it (copied behind it on
+        // the download stream): no blocking read that would wait for the
+        // frame queued since
+        if (c->h_err_async[k]) {
+            c->h_err_async[k] = 0;
+            SR_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st), "cudaMemsetAsync(err)");
+            snprintf(c->err, sizeof(c->err), "a bounded device wait for a cost-row copy ran out");
+            SR_LOG(1, "%s", c->err);
+            return SR_ERR_TIMEOUT;
+        }
         // upload after that frame's kernels have read the slot's images
         SR_TRY(c, cudaStreamWaitEvent(c->up, c->ev_comp[k], 0), "cudaStreamWaitEvent");
     }
@@ -828,6 +839,9 @@ sr_status sr_match_host_async(sr_ctx *c, const uint8_t *h_left, const uint8_t *h
     SR_TRY(c, cudaStreamWaitEvent(c->down, c->ev_comp[k], 0), "cudaStreamWaitEvent");
     SR_TRY(c, cudaMemcpyAsync(h_disp, dd, npx * sizeof(float), cudaMemcpyDeviceToHost, c->down),
            "D2H disp");
+    SR_TRY(c, cudaMemcpyAsync(&c->h_err_async[k], c->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                              c->down),
+           "D2H err");
     SR_TRY(c, cudaEventRecord(c->ev_down[k], c->down), "cudaEventRecord");
     // the next match on this slot writes dd: after this download
     c->slot = k ^ 1;

@@ -53,6 +53,7 @@ struct sr_ctx {
     cudaEvent_t ev_up[2] = {}, ev_comp[2] = {}, ev_down[2] = {};
     int slot = 0;
     long long frames_queued = 0;
+    int *h_err_async = nullptr;   // pinned [2]: the error word after each slot's frame
     int debug = 0;
     int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
     bool matched = false, agg_valid = false;

@@ -306,6 +306,43 @@ def test_bounded_wait_reports_timeout_and_gpu_stays_usable():
         np.testing.assert_array_equal(wta.cpu().numpy(), good["wta"])
 
 
+def test_streaming_call_reports_timeout_without_blocking_read():
+    """sr_match_host_async reads each frame's error word from a copy queued
+    behind the frame's download: two frames whose bounded waits run out make
+    the third call return SR_ERR_TIMEOUT, and the stream then goes on with
+    correct frames."""
+    import torch
+    from paper_1807_07433_gb300 import sr
+    w = CASES[0]
+    left, right, _ = synth.make_pair(w.scene)
+    H, W = left.shape
+    hl, hr = torch.from_numpy(left).pin_memory(), torch.from_numpy(right).pin_memory()
+    with sr.Matcher(W, H, w.D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh,
+                    stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        want = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        sr.sr_match_host(m.ctx, hl, hr, want)
+        outs = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(6)]
+        sr.sr_set_debug(m.ctx, sr.SR_DEBUG_WITHHOLD_ROW)
+        sr.sr_match_host_async(m.ctx, hl, hr, outs[0])
+        sr.sr_match_host_async(m.ctx, hl, hr, outs[1])
+        with pytest.raises(sr.SrError) as e:
+            sr.sr_match_host_async(m.ctx, hl, hr, outs[2])
+        assert e.value.status == sr.SR_ERR_TIMEOUT
+        sr.sr_set_debug(m.ctx, 0)
+        done = []
+        for k in range(2, 6):
+            try:
+                sr.sr_match_host_async(m.ctx, hl, hr, outs[k])
+                done.append(k)
+            except sr.SrError as e2:   # the second withheld frame may report too
+                assert e2.status == sr.SR_ERR_TIMEOUT and k == 2
+        sr.sr_synchronize(m.ctx)
+        assert len(done) >= 3
+        for k in done:
+            np.testing.assert_array_equal(outs[k].numpy(), want.numpy())
+
+
 EXTREME = [
     # the widest frame the ABI accepts, fewer rows than the NCC block
     synth.small(16384, 5, D=64, ncc_r=3, agg_r=5, seed=51, alpha1=0.02),
