@@ -58,6 +58,43 @@ def run_case(w, vol_dtype):
     return out
 
 
+BATCH_SIZES = [(96, 40), (203, 77), (150, 61)]
+BATCH_VARIANTS = (0, 4, 7)   # persistent, descriptor-driven per pair, sr_match's kernels
+
+
+def run_batch(variant):
+    """A mixed-size batch (D = 64, FP32) under one schedule, then one plain
+    match (launches inside the batch's graph are checked by the next plain
+    launch of their kernel files); returns the pairs' outputs."""
+    import torch
+    keep, descs, outs = [], [], []
+    for k, (W, H) in enumerate(BATCH_SIZES):
+        sc = synth.Scene(W, H, 12.0 + k, 0.05, 1, False, 3000 + k)
+        left, right, _ = synth.make_pair(sc)
+        tl, tr = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+        disp = torch.full((H, W), -3.0, device="cuda")
+        wta = torch.full((H, W), -3, dtype=torch.int16, device="cuda")
+        keep += [tl, tr]
+        outs.append((disp, wta))
+        descs.append(sr.make_pair_desc(tl, tr, disp, sc.alpha0, sc.alpha1, 8.0, wta))
+    with sr.Matcher(8, 8, 64, 3, 5, 4.0, 12.0, stream=torch.cuda.current_stream()) as m:
+        sr.sr_set_batch_schedule(m.ctx, variant)
+        sr.sr_match_batch(m.ctx, descs)
+        sr.sr_match_batch(m.ctx, descs)   # a replay of the graph
+        sr.sr_synchronize(m.ctx)
+    w = synth.small(64, 16, D=64, ncc_r=3, agg_r=5, seed=3100)
+    left, right, _ = synth.make_pair(w.scene)
+    with sr.Matcher(64, 16, 64, 3, 5, 4.0, 12.0, stream=torch.cuda.current_stream()) as m:
+        m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
+        m.match(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda())
+        torch.cuda.synchronize()
+    res = {}
+    for k, (d, wt) in enumerate(outs):
+        res[f"disp{k}"] = d.cpu().numpy()
+        res[f"wta{k}"] = wt.cpu().numpy()
+    return res
+
+
 def main(path):
     import torch
     sr.load(sr.CHECK_LIB_PATH)
@@ -68,6 +105,11 @@ def main(path):
             res[f"{name}.{k}"] = v
         st, site, index, unit, count = sr.sr_bounds_report()
         res[f"{name}.report"] = np.array([st, site, index, count], dtype=np.int64)
+    for v in BATCH_VARIANTS:
+        for k, a in run_batch(v).items():
+            res[f"batch{v}.{k}"] = a
+        st, site, index, unit, count = sr.sr_bounds_report()
+        res[f"batch{v}.report"] = np.array([st, site, index, count], dtype=np.int64)
     # self-test: one recorded offence (site 399, index -1), no memory access
     w = synth.C1
     left, right, _ = synth.make_pair(w.scene)

@@ -2,10 +2,11 @@
 
 The checked library runs the match path -- the stage-parity scenes (ragged,
 tiny and degenerate sizes), the 1280x720x64 frame at FP32 and FP16, the
-restricted search, row bands and reconstruction -- in a child process. Every
-checked index stays inside its buffer (sr_bounds_report: SR_OK after each
-case), and every output equals the release library's bit for bit (the checks
-change no arithmetic). A self-test flag makes the checked reconstruction
+restricted search, row bands, reconstruction, and a mixed-size batch under
+the persistent, per-pair and sr_match-kernel schedules -- in a child
+process. Every checked index stays inside its buffer (sr_bounds_report:
+SR_OK after each case), and every output equals the release library's bit
+for bit (the checks change no arithmetic). A self-test flag makes the checked reconstruction
 record one offence without any memory access: the call returns
 SR_ERR_BOUNDS, the report gives its site and index, and the context works on.
 """
@@ -53,6 +54,19 @@ def test_outputs_equal_release_build(checked):
             assert np.array_equal(got.view(np.uint8), v.view(np.uint8)), (name, k)
             ran += 1
     assert ran >= 3 * len(bounds_child.CASES)
+
+
+def test_batch_schedules_in_range_and_equal(checked):
+    """The persistent, descriptor-driven and per-pair batch schedules: no
+    offence, and the same outputs as the release library's."""
+    from paper_1807_07433_gb300 import sr
+    import bounds_child
+    for v in bounds_child.BATCH_VARIANTS:
+        st, site, index, count = checked[f"batch{v}.report"]
+        assert st == sr.SR_OK and count == 0, (v, site, index, count)
+        ref = bounds_child.run_batch(v)
+        for k, a in ref.items():
+            assert np.array_equal(checked[f"batch{v}.{k}"].view(np.uint8), a.view(np.uint8)), (v, k)
 
 
 def test_selftest_reports_through_the_abi(checked):
