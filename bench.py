@@ -50,15 +50,24 @@ def agg_flops_per_launch(W, H, D, agg_r):
 AGG_SOURCES = ("k_agg.cuh", "k_agg_d64_f32.cu")
 
 
+def _code_only(text: str) -> str:
+    """C++ source without // and /* */ comments and without blank space, so
+    that an edit of a comment leaves the hash of the code alone."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def _kernel_sha() -> str:
-    """Hash of the sources of the 1280x720x64 FP32 aggregation kernel."""
+    """Hash of the code (comments dropped) of the 1280x720x64 FP32
+    aggregation kernel's sources."""
     h = hashlib.sha256()
     for name in AGG_SOURCES:
         path = os.path.join(ROOT, "paper_1807_07433_gb300", "csrc", name)
         if not os.path.exists(path):
             return "missing"
-        with open(path, "rb") as f:
-            h.update(f.read())
+        with open(path) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -17,11 +17,12 @@
 //     word instead of hanging.  In the same step the CTA computes the weights
 //     that row needs -- tap row dy = y - v of each of the 4 output rows --
 //     into a second double-buffered ring laid out [row][dx][pixel], so one
-//     128-bit load gives one tap's weight for four adjacent pixels.  Each
-//     weight is computed exactly once, and shared memory stays ~36 KB per
+//     load gives one tap's weight for the lane's adjacent pixels.  Each
+//     weight is computed exactly once, and shared memory stays ~38 KB per
 //     CTA, so four CTAs (16 warps) fit on an SM;
 //   * lane = 4 disparities of a block of 4 x 4 pixels (8 disparities of
-//     2 x 4 pixels for FP32 costs at D = 64); the lanes of a pixel group
+//     2 x 4 pixels for FP32 costs at D = 64 and in the band kernel's
+//     padded slices); the lanes of a pixel group
 //     read the same weights (a broadcast) and together one cost column
 //     (16-byte loads, conflict-free);
 //   * each thread accumulates 64 sums, held as 32 pairs of disparities that
@@ -31,12 +32,12 @@
 //     lane's pixels and every output row that uses the source row (32
 //     independent paired multiply-adds);
 //   * epilogue: the sums are transposed through shared memory (over the
-//     rings; 16-byte stores, rows of D + 4) so that each lane scans the D
-//     costs of one pixel, four per load: argmax (ties to the smallest d),
-//     then Eq. 12 on the neighbours of the winner.  The
-//     normalisation by sum_k w_k is a positive per-pixel scale, which
-//     changes neither the argmax nor the parabola vertex, so it is applied
-//     only when the aggregated volume is exported.
+//     rings; 16-byte stores, rows of D + 4; the band kernel keeps rows of
+//     D + 1) so that each lane scans the D costs of one pixel, four per
+//     load: argmax (ties to the smallest d), then Eq. 12 on the neighbours
+//     of the winner.  The normalisation by sum_k w_k is a positive
+//     per-pixel scale, which changes neither the argmax nor the parabola
+//     vertex, so it is applied only when the aggregated volume is exported.
 #pragma once
 #include <cuda.h>
 

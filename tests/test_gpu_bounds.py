@@ -6,9 +6,10 @@ restricted search, row bands, reconstruction, and a mixed-size batch under
 the persistent, per-pair and sr_match-kernel schedules -- in a child
 process. Every checked index stays inside its buffer (sr_bounds_report:
 SR_OK after each case), and every output equals the release library's bit
-for bit (the checks change no arithmetic). A self-test flag makes the checked reconstruction
-record one offence without any memory access: the call returns
-SR_ERR_BOUNDS, the report gives its site and index, and the context works on.
+for bit (the checks change no arithmetic). A self-test flag makes the
+checked reconstruction record one offence without any memory access: the
+call returns SR_ERR_BOUNDS, the report gives its site and index, and the
+context works on.
 """
 import os
 import subprocess
