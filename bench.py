@@ -298,7 +298,9 @@ def run_ours(args, w):
     disp = torch.empty((H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    m = sr.Matcher(W, H, D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh, stream=stream)
+    vol = {"f32": sr.SR_VOL_F32, "f16": sr.SR_VOL_F16, "bf16": sr.SR_VOL_BF16}[args.volume]
+    m = sr.Matcher(W, H, D, w.ncc_r, w.agg_r, w.gamma_d, w.gamma_r, w.lr_thresh, vol_dtype=vol,
+                   stream=stream)
     m.set_plane(w.scene.alpha0, w.scene.alpha1, w.delta)
     kpm = sr.sr_kernels_per_match(m.ctx)
 
@@ -387,7 +389,8 @@ def run_ours(args, w):
                 "paper_1807_07433_gb300/synth.py, seed 2); stands in for the paper's ZED road data",
         "config": {"workload": w.name, "W": W, "H": H, "D": D, "ncc_window": 2 * w.ncc_r + 1,
                    "bilateral_window": 2 * w.agg_r + 1, "gamma_d": w.gamma_d,
-                   "gamma_r": w.gamma_r, "delta": w.delta, "form": "staged fp32 volumes",
+                   "gamma_r": w.gamma_r, "delta": w.delta,
+                   "form": "staged " + {"f32": "fp32", "f16": "fp16", "bf16": "bf16"}[args.volume] + " volumes",
                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB memset)",
                    "parallelism": f"replicas x{ws} (independent frames)"},
         "roofline": {"bound": "alu", "kernel": "k_agg_wta (reference view)",
@@ -395,7 +398,7 @@ def run_ours(args, w):
                      "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                      "flops_per_launch": flops, "launch_ms": round(agg_avg_ms, 5),
-                     "traffic": _stored_traffic()},
+                     "traffic": _stored_traffic() if args.volume == "f32" else None},
         "stages_ms": stages,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 4 * W * H,
@@ -1085,6 +1088,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16/BF16 and batched forms of the default line")
+    ap.add_argument("--volume", choices=("f32", "f16", "bf16"), default="f32",
+                    help="storage type of the cost volumes of the main line (arithmetic stays FP32)")
     ap.add_argument("--form-steps", type=int, default=200,
                     help="timed steps of each extra form (default 200)")
     ap.add_argument("--report", choices=("precision", "batch", "adjoint", "sweep", "fit", "accuracy",
