@@ -42,6 +42,7 @@
 #include <cuda.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "sr_internal.cuh"
 
@@ -168,6 +169,7 @@ struct AggCfg {
     static constexpr size_t SMEM_SINGLE = SMEM - sizeof(int) * kStartSmem;
     static_assert(single_for(RING) == SMEM_SINGLE, "shared-memory layouts disagree");
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
+    static_assert(kAggTY == 4, "band counters assume tiles of 4 rows");
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -280,7 +282,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
                                          int *__restrict__ err, long long wait_cycles,
                                          int withhold_last, int x0, int y0,
                                          const void *tmap = nullptr, int dlo = 0,
-                                         const AggWin &win = AggWin()) {
+                                         const AggWin &win = AggWin(), int pdl = 0) {
     using C = AggCfg<R, D, VT, SH, BAND>;
     float *smem = sm.epi();                      // epilogue view
     VT *ring = sm.ring();                        // [2][TXE][D] cost rows
@@ -386,6 +388,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
     // the others; in a persistent CTA the barrier before this tile ordered
     // the previous epilogue's reads of this memory)
     if (tid == 0) {
+        if (pdl == 1) {   // the volume's producer grid is complete (see pdl_trigger)
+            pdl_wait();
+            asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         issue_row(0);
     }
@@ -419,6 +425,9 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             make_weights(j, std::integral_constant<bool, false>());
     };
     __syncthreads();
+    // (pdl == 1) every thread is past thread 0's wait for the volume's
+    // producer: a programmatic dependent may launch once all CTAs are here
+    if (pdl == 1) pdl_trigger();
     if (C::WSL == 2) weights_of_row(0);
     __syncthreads();
 
@@ -610,6 +619,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
                 }
             }
         }
+    if (pdl == 2) pdl_wait();   // the target labels' grid is complete (see pdl_trigger)
     __syncthreads();
     for (int pw = lane; pw < C::PPG * C::G; pw += 32) {
         const int g = pw / C::PPG, py = (pw % C::PPG) / PX, px = pw % PX;
@@ -697,7 +707,7 @@ k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
           const float *__restrict__ gf, int W, int H, float kd, float kr,
           int16_t *__restrict__ lbl, float *__restrict__ dsub, float *__restrict__ agg,
           int *__restrict__ err, long long wait_cycles, int withhold_last, AggWin win,
-          int vpitch) {
+          int vpitch, int pdl) {
     // restricted search: tiles of the band kernel are not this kernel's
     if (WIN && win.band && win.band[blockIdx.y * gridDim.x + blockIdx.x] >= 0) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -706,7 +716,7 @@ k_agg_wta(const VT *__restrict__ vol, const uint8_t *__restrict__ gl, int pitch,
     unsigned ph = 0;
     agg_tile<R, D, GU8, VT, false, WIN>(sm, ph, vol, vpitch, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg,
                                         err, wait_cycles, withhold_last, blockIdx.x * kAggTX,
-                                        blockIdx.y * kAggTY, nullptr, 0, win);
+                                        blockIdx.y * kAggTY, nullptr, 0, win, pdl);
 }
 
 // Target view from the extended reference volume (see AggCfg): the guide is
@@ -715,7 +725,7 @@ template <int R, int D, typename VT>
 __global__ void __launch_bounds__(AggCfg<R, D, VT, true>::NT, AggCfg<R, D, VT, true>::MINB)
 k_agg_shear(const __grid_constant__ CUtensorMap tmap, int vpitch, const float *__restrict__ gf,
             int W, int H, float kd, float kr, int16_t *__restrict__ lbl, float *__restrict__ agg,
-            int *__restrict__ err, long long wait_cycles, int withhold_last) {
+            int *__restrict__ err, long long wait_cycles, int withhold_last, int pdl) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const AggSmem<R, D, VT, true> sm{smem_raw};
     agg_init_barriers(sm);
@@ -723,7 +733,7 @@ k_agg_shear(const __grid_constant__ CUtensorMap tmap, int vpitch, const float *_
     agg_tile<R, D, false, VT, false, false, true>(sm, ph, nullptr, vpitch, nullptr, 0, gf, W, H,
                                                   kd, kr, lbl, nullptr, agg, err, wait_cycles,
                                                   withhold_last, blockIdx.x * kAggTX,
-                                                  blockIdx.y * kAggTY, &tmap);
+                                                  blockIdx.y * kAggTY, &tmap, 0, AggWin(), pdl);
 }
 
 // Band kernel of the restricted search: the tile's kBandD-disparity slice
@@ -788,6 +798,24 @@ k_agg_batch(const PairDesc *__restrict__ pairs, const int *__restrict__ start, i
     }
 }
 
+// Launch k on st; with pdl, as a programmatic dependent of the stream's
+// previous kernel (it may start before that kernel ends; see pdl_trigger).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args &&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <int R, int D, typename VT, bool WIN>
 cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const float *gf, int W,
                          int H, float kd, float kr, int16_t *lbl, float *dsub, float *agg,
@@ -798,9 +826,12 @@ cudaError_t agg_launch_t(const VT *vol, const uint8_t *gl, int pitch, const floa
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_SINGLE);
     if (e != cudaSuccess) return e;
-    k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(vol, gl, pitch, gf, W, H, kd, kr, lbl, dsub, agg, dbg.err,
-                                    dbg.wait_cycles, dbg.withhold_last, win, vpitch);
-    cudaError_t el = cudaGetLastError();
+    // the fused L-R check waits for the target view's grid (see pdl_trigger)
+    const int pdl = dbg.pdl && win.post.disp ? 2 : 0;
+    e = launch_k(pdl != 0, k, grid, dim3(C::NT), C::SMEM_SINGLE, st, vol, gl, pitch, gf, W, H, kd,
+                 kr, lbl, dsub, agg, dbg.err, dbg.wait_cycles, dbg.withhold_last, win, vpitch,
+                 pdl);
+    cudaError_t el = e != cudaSuccess ? e : cudaGetLastError();
     SR_OOB_COLLECT(el, st);
     return el;
 }
@@ -815,9 +846,10 @@ cudaError_t agg_shear_launch_t(const CUtensorMap &tmap, int vpitch, const float 
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM_SINGLE);
     if (e != cudaSuccess) return e;
-    k<<<grid, C::NT, C::SMEM_SINGLE, st>>>(tmap, vpitch, gf, W, H, kd, kr, lbl, agg, dbg.err,
-                                    dbg.wait_cycles, dbg.withhold_last);
-    cudaError_t el = cudaGetLastError();
+    const int pdl = dbg.pdl ? 1 : 0;   // the first cost-row copy waits for the NCC grid
+    e = launch_k(pdl != 0, k, grid, dim3(C::NT), C::SMEM_SINGLE, st, tmap, vpitch, gf, W, H, kd,
+                 kr, lbl, agg, dbg.err, dbg.wait_cycles, dbg.withhold_last, pdl);
+    cudaError_t el = e != cudaSuccess ? e : cudaGetLastError();
     SR_OOB_COLLECT(el, st);
     return el;
 }

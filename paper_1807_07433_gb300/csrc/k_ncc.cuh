@@ -209,6 +209,7 @@ k_ncc(const uint8_t *__restrict__ left, int pitch, const float *__restrict__ rw,
       const float *__restrict__ mu_r, const float *__restrict__ inv_r, int W, int H,
       VT *__restrict__ vol, int Wo, const int2 *__restrict__ range) {
     __shared__ NccSmem<RN, D> sm;
+    pdl_trigger();   // a programmatic dependent may launch once every CTA is here
     int dlo = 0, dhi = D - 1;
     if (range) {   // restricted search: the disparities the tile's readers need
         const int2 r = range[blockIdx.y * gridDim.x + blockIdx.x];

@@ -581,7 +581,11 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
                "ncc");
     }
     SR_TRY(c, mark(), "cudaEventRecord");
-    const sr::AggDebug dbg = agg_debug(c);
+    sr::AggDebug dbg = agg_debug(c);
+    // each aggregation starts while its predecessor drains (programmatic
+    // dependent launch, see sr::pdl_trigger); not while stage events sit
+    // between the kernels
+    dbg.pdl = !prof;
     // target view first: the reference-view kernel runs the L-R check and
     // the post-processing in its epilogue, on the finished target labels
     {

@@ -164,6 +164,22 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
                        const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
                        cudaStream_t st, const int2 *range = nullptr, int Wo = 0);
 
+// Overlap of sr_match's kernels by programmatic dependent launch: the two
+// aggregations are launched as programmatic dependents, so each starts
+// while its predecessor drains (once every CTA of the predecessor has
+// triggered).  The NCC kernel triggers at its start.  The target-view
+// aggregation's first cost-row copy waits for the NCC grid (thread 0,
+// griddepcontrol.wait) and its CTAs trigger only after that wait, so the
+// reference view starts only once the NCC volume is complete; the reference
+// view then runs its main loop and waits for the target-view grid (its
+// labels) only before the L-R check of its epilogue.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Bounded-wait settings of the aggregation kernel.  err (nullable) receives 1
 // when a wait for a cost-row copy runs out after wait_cycles SM clocks;
 // withhold_last = 1 withholds the copy of the last source row of every tile
@@ -172,7 +188,9 @@ struct AggDebug {
     int *err = nullptr;
     long long wait_cycles = 2000000000LL;   // ~1 s at 2 GHz
     int withhold_last = 0;
+    int pdl = 0;   // launch as a programmatic dependent (see pdl_trigger)
 };
+
 
 // Restricted search (the paper's Sec. IV plan): pixel p searches only
 // [max(0, c - radius), min(dfull - 1, c + radius)] around its centre c
@@ -208,6 +226,8 @@ constexpr int kAggTileX = 32, kAggTileY = 4;   // aggregation tile (pixels)
 // int16, dsub [H][W] float (nullable) and, for inspection, the normalised
 // aggregated volume agg [H][W][D] (nullable).  vpitch: pixels per row of
 // the volume (0: W; W + D - 1 for the extended reference volume).
+// dbg.pdl: launch as a programmatic dependent of the target view; the fused
+// L-R check waits for it (see pdl_trigger).
 cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pitch,
                        const float *guide_f32, int W, int H, int D, int agg_r, float gamma_d,
                        float gamma_r, int16_t *lbl, float *dsub, float *agg,
@@ -218,6 +238,8 @@ cudaError_t launch_agg(const void *vol, int vt, const uint8_t *guide_u8, int pit
 // (launch_ncc with Wo = W + D - 1): pixel u at disparity d takes column
 // u + d, through the 2-D tensor map tmap of encode_shear_map.  Guide: the
 // warped target.  Writes lbl [H][W] and, for inspection, agg (nullable).
+// dbg.pdl: launch as a programmatic dependent of the NCC kernel (see
+// pdl_trigger).
 cudaError_t launch_agg_shear(const void *tmap, int vt, const float *guide_f32, int W, int H,
                              int D, int agg_r, float gamma_d, float gamma_r, int16_t *lbl,
                              float *agg, const AggDebug &dbg, cudaStream_t st);
