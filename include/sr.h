@@ -135,12 +135,16 @@ sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, i
  * [y0, y1) of the W x H frame the context was created for, equal bit for bit
  * to those rows of sr_match on the whole frame.  Every step of the path is
  * row-local up to a window: an NCC block (Eq. 3) reaches ncc_radius rows and
- * a bilateral window (Eq. 8) agg_radius rows, so a band needs only the halo
- * rows r0 = max(0, y0 - h) .. r1 - 1 = min(H, y1 + h) - 1, h = ncc_radius +
- * agg_radius, of both images; it takes the plane of its rows in the frame
- * (row v shifted by alpha0 + alpha1*v - delta, v counted from the frame's
- * first row).  This is the row partition of a frame over several GPUs: each
- * holds its band and halo rows, and the bands need no exchange.
+ * a bilateral window (Eq. 8) agg_radius rows, so a band needs only halo rows
+ * of both images, r0 .. r1 - 1 as sr_band_rows gives them: r1 = min(H, y1 +
+ * h), h = ncc_radius + agg_radius, and r0 <= y0 - h (or 0), back to the first
+ * row of the NCC kernel's row segment that holds row y0 - agg_radius, less
+ * ncc_radius (the NCC kernel keeps window sums per segment of image rows, and
+ * their rounding starts at the segment's first row).  The band takes the
+ * plane of its rows in the frame (row v shifted by alpha0 + alpha1*v - delta,
+ * v counted from the frame's first row).  This is the row partition of a
+ * frame over several GPUs: each holds its band and halo rows, and the bands
+ * need no exchange.
  *   d_left_rows, d_right_rows  image rows r0..r1-1 (pointers to row r0),
  *                              row pitch pitch_bytes (>= W)
  *   y0, y1                     0 <= y0 < y1 <= H
@@ -149,7 +153,7 @@ sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, i
  *   d_wta_rows_or_null         optional (y1 - y0) x W int16: the same rows
  *                              of sr_match's d_wta_or_null
  * The halo rows are matched too (and discarded), so a band costs its rows
- * plus up to 2h rows.  Uses the context's scratch (sr_get_buffer reports
+ * plus up to 2h rows and one NCC row segment (sr_band_rows).  Uses the context's scratch (sr_get_buffer reports
  * SR_ERR_STATE afterwards); the first call allocates 6*W*H bytes of band
  * output and builds a tensor map for bands of r1 - r0 rows (rebuilt when
  * that count changes).  Asynchronous.  Errors: SR_ERR_INVALID_ARG,
@@ -157,6 +161,11 @@ sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, i
 sr_status sr_match_rows(sr_ctx *ctx, const uint8_t *d_left_rows, const uint8_t *d_right_rows,
                         int pitch_bytes, int y0, int y1, float *d_disp_rows,
                         int16_t *d_wta_rows_or_null);
+
+/* The image rows [*r0, *r1) that sr_match_rows reads for output rows
+ * [y0, y1) (see there).  Host only, no GPU work.  Errors: SR_ERR_INVALID_ARG
+ * for null arguments or rows outside 0 <= y0 < y1 <= H. */
+sr_status sr_band_rows(const sr_ctx *ctx, int y0, int y1, int *r0, int *r1);
 
 /* Restricted search: sr_match with every pixel of both views searching only
  * the window [c - radius, c + radius] (clamped to 0..D-1) around its centre

@@ -45,9 +45,13 @@ def halo(ncc_r: int, agg_r: int) -> int:
     return int(ncc_r) + int(agg_r)
 
 
-def plan(H: int, n: int, ncc_r: int, agg_r: int) -> list[Band]:
+def plan(H: int, n: int, ncc_r: int, agg_r: int, read_rows=None) -> list[Band]:
     """Split H rows into n bands of floor(H/n) or ceil(H/n) rows (the first
-    H mod n bands take one more), each with its halo rows."""
+    H mod n bands take one more), each with its halo rows: by default the
+    h = ncc_r + agg_r rows the windows reach; read_rows(y0, y1) -> (r0, r1)
+    gives them instead where the matcher needs more (the GPU library's
+    sr_band_rows, whose NCC kernel keeps window sums per segment of rows and
+    so reads back to the start of a segment)."""
     if n < 1 or H < n:
         raise ValueError(f"cannot split {H} rows into {n} non-empty bands")
     h = halo(ncc_r, agg_r)
@@ -56,7 +60,10 @@ def plan(H: int, n: int, ncc_r: int, agg_r: int) -> list[Band]:
     for k in range(n):
         rows = base + (1 if k < extra else 0)
         y0, y1 = y, y + rows
-        out.append(Band(y0, y1, max(0, y0 - h), min(H, y1 + h)))
+        r0, r1 = read_rows(y0, y1) if read_rows else (max(0, y0 - h), min(H, y1 + h))
+        if not (0 <= r0 <= max(0, y0 - h) and r1 == min(H, y1 + h)):
+            raise ValueError(f"rows [{r0}, {r1}) do not hold band [{y0}, {y1}) and its halo")
+        out.append(Band(y0, y1, r0, r1))
         y = y1
     return out
 

@@ -100,6 +100,25 @@ cudaError_t launch_agg_batch_d64_bf16(bool, const PairDesc *, const int *, int, 
 int ncc_occ_d64_bf16(int);
 int agg_occ_d64_bf16(int);
 
+cudaError_t launch_ncc_sl_d16_f32(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d16_f32(int);
+cudaError_t launch_ncc_sl_d16_f16(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d16_f16(int);
+cudaError_t launch_ncc_sl_d16_bf16(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d16_bf16(int);
+cudaError_t launch_ncc_sl_d32_f32(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d32_f32(int);
+cudaError_t launch_ncc_sl_d32_f16(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d32_f16(int);
+cudaError_t launch_ncc_sl_d32_bf16(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d32_bf16(int);
+cudaError_t launch_ncc_sl_d64_f32(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d64_f32(int);
+cudaError_t launch_ncc_sl_d64_f16(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d64_f16(int);
+cudaError_t launch_ncc_sl_d64_bf16(const uint8_t *, const uint8_t *, int, int, int, int, int, double, double, double, const float *, const float *, void *, int, int, cudaStream_t);
+int ncc_sl_occ_d64_bf16(int);
+
 bool ncc_supported(int D, int ncc_r) {
     return (D == 16 || D == 32 || D == 64) && ncc_r >= 1 && ncc_r <= 5;
 }
@@ -125,6 +144,18 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
         case 16: SR_VT_DISPATCH(launch_ncc, 16, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, Wo, st, range)
         case 32: SR_VT_DISPATCH(launch_ncc, 32, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, Wo, st, range)
         case 64: SR_VT_DISPATCH(launch_ncc, 64, vt, target, left, pitch, rw, mu_l, inv_l, mu_r, inv_r, W, H, ncc_r, vol, Wo, st, range)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_ncc_sl(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
+                          int D, int ncc_r, int row0, double alpha0, double alpha1, double delta,
+                          const float *inv_l, const float *inv_r, void *vol, int vt, int Wo,
+                          int seg, cudaStream_t st) {
+    switch (D) {
+        case 16: SR_VT_DISPATCH(launch_ncc_sl, 16, vt, left, right, pitch, W, H, ncc_r, row0, alpha0, alpha1, delta, inv_l, inv_r, vol, Wo, seg, st)
+        case 32: SR_VT_DISPATCH(launch_ncc_sl, 32, vt, left, right, pitch, W, H, ncc_r, row0, alpha0, alpha1, delta, inv_l, inv_r, vol, Wo, seg, st)
+        case 64: SR_VT_DISPATCH(launch_ncc_sl, 64, vt, left, right, pitch, W, H, ncc_r, row0, alpha0, alpha1, delta, inv_l, inv_r, vol, Wo, seg, st)
         default: return cudaErrorInvalidValue;
     }
 }
@@ -227,6 +258,52 @@ int agg_batch_occupancy(int D, int agg_r, int vt) {
         case 64: SR_OCC_DISPATCH(agg_occ, 64, vt, agg_r)
         default: return 0;
     }
+}
+
+int ncc_sl_occupancy(int D, int ncc_r, int vt) {
+    switch (D) {
+        case 16: SR_OCC_DISPATCH(ncc_sl_occ, 16, vt, ncc_r)
+        case 32: SR_OCC_DISPATCH(ncc_sl_occ, 32, vt, ncc_r)
+        case 64: SR_OCC_DISPATCH(ncc_sl_occ, 64, vt, ncc_r)
+        default: return 0;
+    }
+}
+
+// Segment length: a CTA of launch_ncc_sl owns 4096/D columns and seg rows,
+// and spends about seg + ncc_r + 2 row steps (the window's first 2 ncc_r + 1
+// rows are only added).  Model: an SM holding L CTAs of a launch takes
+// L * (seg + ncc_r + 2) / min(L, resident, 3) steps (its throughput saturates
+// at three resident CTAs); the shortest model time wins, the longer segment
+// on ties.  Deterministic per (frame size, D, radius, device): the resident
+// count is the kernel's launch bound, not a measured occupancy, which a
+// bounds-checked build would change.
+int ncc_segment(int W, int H, int D, int ncc_r, int vt) {
+    static int env = -1;
+    if (env < 0) {
+        const char *e = getenv("SR_NCC_SEG");
+        const int v = e ? atoi(e) : 0;
+        env = (v >= 1 && v <= kNslMaxSeg) ? v : 0;
+    }
+    if (env > 0) return env;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    (void)vt;
+    const int occ = kNslResident;   // a constant, so that every build picks the same segments
+    const int tx = 4096 / D;
+    const long long nx = (W + D - 1 + tx - 1) / tx;
+    const int hi = std::min(std::max(H, 1), kNslMaxSeg), lo = std::min(hi, 8);
+    int best = hi;
+    double best_t = 1e300;
+    for (int seg = hi; seg >= lo; --seg) {
+        const long long nseg = (H + seg - 1) / seg;
+        const long long L = (nx * nseg + sms - 1) / sms;
+        const long long conc = std::min<long long>(std::min<long long>(L, occ), 3);
+        const double t = (double)L * (seg + ncc_r + 2) / (double)conc;
+        if (t < best_t) { best_t = t; best = seg; }
+    }
+    return best;
 }
 
 }  // namespace sr
@@ -437,6 +514,7 @@ sr_status sr_create(const sr_params *params, void *cuda_stream, sr_ctx **out) {
         delete c;
         return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
     }
+    c->ncc_seg = sr::ncc_segment(p.width, p.height, p.max_disp, p.ncc_radius, (int)p.vol_dtype);
     *out = c;
     SR_LOG(2, "context %dx%d, D %d, NCC %dx%d, bilateral %dx%d, volume type %d on device %d",
            p.width, p.height, p.max_disp, 2 * p.ncc_radius + 1, 2 * p.ncc_radius + 1,
@@ -575,9 +653,9 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
         // one extended reference volume holds both views (target c(u,d) =
         // extended reference c(u+d,d))
         NvtxRange r("ncc");
-        SR_TRY(c, sr::launch_ncc(false, d_left, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                                 c->inv_r, W, H, D, p.ncc_radius, c->vol_l, p.vol_dtype, st,
-                                 nullptr, WE),
+        SR_TRY(c, sr::launch_ncc_sl(d_left, d_right, pitch_bytes, W, H, D, p.ncc_radius, 0,
+                                    c->alpha0, c->alpha1, c->delta, c->inv_l, c->inv_r, c->vol_l,
+                                    p.vol_dtype, WE, c->ncc_seg, st),
                "ncc");
     }
     SR_TRY(c, mark(), "cudaEventRecord");
@@ -618,6 +696,25 @@ sr_status sr_match(sr_ctx *c, const uint8_t *d_left, const uint8_t *d_right, int
     return SR_OK;
 }
 
+// Image rows [r0, r1) that the band of output rows [y0, y1) reads: the rows
+// its bilateral windows (agg_radius) and NCC blocks (ncc_radius) reach, and
+// above them back to the first row of the NCC segment of its first cost row
+// minus ncc_radius, where that segment's window sums start in the whole
+// frame too (see launch_ncc_sl).
+static void band_read_rows(const sr_ctx *c, int y0, int y1, int *r0, int *r1) {
+    const sr_params &p = c->p;
+    const int first_cost = std::max(0, y0 - p.agg_radius);
+    const int seg_start = first_cost / c->ncc_seg * c->ncc_seg;
+    *r0 = std::max(0, seg_start - p.ncc_radius);
+    *r1 = std::min(p.height, y1 + p.ncc_radius + p.agg_radius);
+}
+
+sr_status sr_band_rows(const sr_ctx *c, int y0, int y1, int *r0, int *r1) {
+    if (!c || !r0 || !r1 || y0 < 0 || y1 > c->p.height || y0 >= y1) return SR_ERR_INVALID_ARG;
+    band_read_rows(c, y0, y1, r0, r1);
+    return SR_OK;
+}
+
 sr_status sr_match_rows(sr_ctx *c, const uint8_t *d_left_rows, const uint8_t *d_right_rows,
                         int pitch_bytes, int y0, int y1, float *d_disp_rows,
                         int16_t *d_wta_rows_or_null) {
@@ -628,8 +725,9 @@ sr_status sr_match_rows(sr_ctx *c, const uint8_t *d_left_rows, const uint8_t *d_
     const int W = p.width, H = p.height, D = p.max_disp;
     if (y0 < 0 || y1 > H || y0 >= y1) return SR_ERR_INVALID_ARG;
     // the band and the halo rows its NCC blocks and bilateral windows reach
-    const int halo = p.ncc_radius + p.agg_radius;
-    const int r0 = std::max(0, y0 - halo), r1 = std::min(H, y1 + halo), Hs = r1 - r0;
+    int r0 = 0, r1 = 0;
+    band_read_rows(c, y0, y1, &r0, &r1);
+    const int Hs = r1 - r0;
     const size_t npx = (size_t)W * H;
     cudaStream_t st = c->st;
     if (!c->band_disp) {
@@ -653,9 +751,9 @@ sr_status sr_match_rows(sr_ctx *c, const uint8_t *d_left_rows, const uint8_t *d_
                               c->alpha0, c->alpha1, c->delta, r0, c->rw, c->mu_l, c->inv_l,
                               c->mu_r, c->inv_r, c->rowsh, st),
            "prep");
-    SR_TRY(c, sr::launch_ncc(false, d_left_rows, pitch_bytes, c->rw, c->mu_l, c->inv_l, c->mu_r,
-                             c->inv_r, W, Hs, D, p.ncc_radius, c->vol_l, p.vol_dtype, st, nullptr,
-                             WE),
+    SR_TRY(c, sr::launch_ncc_sl(d_left_rows, d_right_rows, pitch_bytes, W, Hs, D, p.ncc_radius,
+                                r0, c->alpha0, c->alpha1, c->delta, c->inv_l, c->inv_r, c->vol_l,
+                                p.vol_dtype, WE, c->ncc_seg, st),
            "ncc");
     const sr::AggDebug dbg = agg_debug(c);
     SR_TRY(c, sr::launch_agg_shear(&c->tmap_band, p.vol_dtype, c->rw, W, Hs, D, p.agg_radius,

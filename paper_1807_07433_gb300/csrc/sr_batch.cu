@@ -1,11 +1,13 @@
 // sr_batch.cu -- sr_match_batch: many stereo pairs of mixed sizes per call.
 //
-// Every stage runs as ONE persistent launch over the flat list of (pair, tile)
-// work items of the whole batch (kernels *_batch in k_pixel.cu, k_ncc.cuh,
-// k_agg.cuh); the seven launches are captured once into a CUDA graph and
-// replayed.  Per call the host only writes the pair descriptors and the
-// per-stage tile prefixes into pinned staging memory and copies them to the
-// device ahead of the graph on the context's stream.
+// Schedule A runs each stage as ONE persistent launch over the flat list of
+// (pair, tile) work items of the whole batch (kernels *_batch in k_pixel.cu,
+// k_ncc.cuh, k_agg.cuh), except the reference NCC volume, which every
+// schedule computes per pair with sr_match's exact-sum kernel (k_ncc_sl.cuh)
+// so that a pair's costs equal sr_match's bit for bit; the launches are
+// captured into a CUDA graph and replayed.  Per call the host writes the pair
+// descriptors and the per-stage tile prefixes into pinned staging memory and
+// copies them to the device ahead of the graph on the context's stream.
 //
 // Two schedules, chosen by a small autotuner when enabled:
 //   A (variants 0-3): one persistent launch per stage over all pairs' tiles,
@@ -18,14 +20,15 @@
 //   B (variants 4-5): per pair, its seven stages as non-persistent launches
 //     (one CTA per tile, as sr_match), the pairs spread over 4 or 8 forked
 //     capture streams, largest first, so that one pair's kernels fill the
-//     tails of another's; still descriptor-driven, so the graph replays with
-//     new images and planes as long as the sequence of sizes repeats;
+//     tails of another's;
 //   C (variants 6-7): per pair, the four kernels of sr_match itself (one
 //     extended NCC volume read by both aggregations) with the pair's pointers
 //     and plane as kernel parameters, on 1 or 4 forked capture streams,
-//     largest first.  The graph holds the parameters, so a call with
-//     other pointers or planes re-captures it and updates the executable graph
-//     in place (cudaGraphExecUpdate; a fresh instantiation if that fails).
+//     largest first.
+// A graph holds per-pair parameters (all of them in C, the reference NCC
+// launches in A and B), so a call with other pointers or planes re-captures
+// it and updates the executable graph in place (cudaGraphExecUpdate; a fresh
+// instantiation if that fails).
 // The tuner times each candidate on the caller's own batch the first time a
 // batch shape is seen and keeps the fastest; with a cache path the choice is
 // stored as one JSON object per line, keyed by GPU name, method parameters
@@ -235,6 +238,19 @@ cudaError_t ensure_capacity(SrBatch *b, int n) {
     return e;
 }
 
+// The reference volume of one pair (W columns) by the exact-sum NCC kernel
+// of sr_match, which every schedule uses for it, so that each pair's
+// reference costs equal those of sr_match on that pair bit for bit.  Its
+// launch holds the pair's pointers and plane, so the graph of any schedule is
+// rebuilt when they change (graph_stale).
+cudaError_t launch_ref_ncc(sr_ctx *c, const sr::PairDesc &P, cudaStream_t st) {
+    const sr_params &p = c->p;
+    const int D = p.max_disp;
+    return sr::launch_ncc_sl(P.left, P.right, P.pitch, P.W, P.H, D, p.ncc_radius, 0, P.alpha0,
+                             P.alpha1, P.delta, P.inv_l, P.inv_r, P.vol_l, p.vol_dtype, P.W,
+                             sr::ncc_segment(P.W, P.H, D, p.ncc_radius, p.vol_dtype), st);
+}
+
 // The seven stage launches of one pair (schedule B) or of the whole batch
 // (schedule A), queued on st.
 cudaError_t launch_pair(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
@@ -247,7 +263,7 @@ cudaError_t launch_pair(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
     cudaError_t e;
     if ((e = sr::launch_warp_batch(d, ps, 1, tp, st)) != cudaSuccess) return e;
     if ((e = sr::launch_stats_batch(d, ps + 2, 1, D, p.ncc_radius, ts, st)) != cudaSuccess) return e;
-    if ((e = sr::launch_ncc_batch(false, d, ps + 4, 1, D, p.ncc_radius, p.vol_dtype, t4, nullptr, st)) != cudaSuccess) return e;
+    if ((e = launch_ref_ncc(c, b->h_desc[k], st)) != cudaSuccess) return e;
     if ((e = sr::launch_ncc_batch(true, d, ps + 4, 1, D, p.ncc_radius, p.vol_dtype, t4, nullptr, st)) != cudaSuccess) return e;
     if ((e = sr::launch_agg_batch(false, d, ps + 4, 1, D, p.agg_radius, p.vol_dtype, p.gamma_d,
                                   p.gamma_r, dbg, t4, nullptr, st)) != cudaSuccess) return e;
@@ -269,8 +285,9 @@ cudaError_t launch_pair_direct(sr_ctx *c, SrBatch *b, int k, cudaStream_t st) {
                              P.rowsh, st)) != cudaSuccess) return e;
     // one extended reference volume for both views, as in sr_match
     const int WE = P.W + D - 1;
-    if ((e = sr::launch_ncc(false, P.left, P.pitch, P.rw, P.mu_l, P.inv_l, P.mu_r, P.inv_r, P.W,
-                            P.H, D, p.ncc_radius, P.vol_l, p.vol_dtype, st, nullptr, WE)) != cudaSuccess) return e;
+    if ((e = sr::launch_ncc_sl(P.left, P.right, P.pitch, P.W, P.H, D, p.ncc_radius, 0, P.alpha0,
+                               P.alpha1, P.delta, P.inv_l, P.inv_r, P.vol_l, p.vol_dtype, WE,
+                               sr::ncc_segment(P.W, P.H, D, p.ncc_radius, p.vol_dtype), st)) != cudaSuccess) return e;
     // target view first; the reference view runs the L-R check and the
     // post-processing in its epilogue, as in sr_match
     if ((e = sr::launch_agg_shear(&b->tmaps[k], p.vol_dtype, P.rw, P.W, P.H, D, p.agg_radius,
@@ -318,7 +335,8 @@ cudaError_t launch_stages(sr_ctx *c, SrBatch *b, int n, int variant, cudaStream_
     if ((e = cudaMemsetAsync(nx, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
     if ((e = sr::launch_warp_batch(b->d_desc, s_pix, n, g_pix, st)) != cudaSuccess) return e;
     if ((e = sr::launch_stats_batch(b->d_desc, s_stat, n, D, p.ncc_radius, g_pix, st)) != cudaSuccess) return e;
-    if ((e = sr::launch_ncc_batch(false, b->d_desc, s_t4, n, D, p.ncc_radius, p.vol_dtype, g_ncc, nx + 0, st)) != cudaSuccess) return e;
+    for (int k = 0; k < n; ++k)
+        if ((e = launch_ref_ncc(c, b->h_desc[k], st)) != cudaSuccess) return e;
     if ((e = sr::launch_ncc_batch(true, b->d_desc, s_t4, n, D, p.ncc_radius, p.vol_dtype, g_ncc, nx + 1, st)) != cudaSuccess) return e;
     if ((e = sr::launch_agg_batch(false, b->d_desc, s_t4, n, D, p.agg_radius, p.vol_dtype, p.gamma_d,
                                   p.gamma_r, dbg, g_agg, nx + 2, st)) != cudaSuccess) return e;
@@ -448,10 +466,10 @@ cudaError_t capture_graph(sr_ctx *c, SrBatch *b, int n, int variant) {
 bool graph_stale(const SrBatch *b, int n, int variant) {
     if (!b->graph || b->graph_n != n || b->graph_variant != variant) return true;
     if (sched_b(variant) && b->graph_sizes != size_signature(b, n)) return true;
-    if (sched_c(variant))
-        return b->graph_desc.size() != (size_t)n ||
-               memcmp(b->graph_desc.data(), b->h_desc, n * sizeof(sr::PairDesc)) != 0;
-    return false;
+    // every schedule's graph holds per-pair launches (the reference NCC
+    // volume at least) with the pairs' pointers and planes
+    return b->graph_desc.size() != (size_t)n ||
+           memcmp(b->graph_desc.data(), b->h_desc, n * sizeof(sr::PairDesc)) != 0;
 }
 
 }  // namespace

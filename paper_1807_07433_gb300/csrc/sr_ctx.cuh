@@ -55,6 +55,7 @@ struct sr_ctx {
     long long frames_queued = 0;
     int *h_err_async = nullptr;   // pinned [2]: the error word after each slot's frame
     int debug = 0;
+    int ncc_seg = 0;                 // row segment of the NCC kernel for this frame size
     int *d_err = nullptr;            // device word set by a kernel whose bounded wait ran out
     bool matched = false, agg_valid = false;
     bool profiling = false, timed = false;

@@ -164,6 +164,27 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
                        const float *inv_r, int W, int H, int D, int ncc_r, void *vol, int vt,
                        cudaStream_t st, const int2 *range = nullptr, int Wo = 0);
 
+constexpr int kNslMaxSeg = 128;   // longest row segment of launch_ncc_sl
+constexpr int kNslResident = 3;   // its CTAs per SM (launch bound)
+
+// Eq. 3 reference volume [H][Wo][D] (Wo = W or the extended W + D - 1)
+// from exact integer window sums (k_ncc_sl.cuh): the left and right images
+// and the plane, not the warped image; inv_l, inv_r are launch_prep's
+// statistics (rows of W + D - 1).  A CTA walks a segment of seg image rows;
+// segments start at the frame's rows that are multiples of seg, row0 being
+// the frame row of the image's first row (a band's), and the costs' last
+// bits depend on seg (ncc_segment gives the one every call on a frame
+// size uses).  seg in 1..128.
+cudaError_t launch_ncc_sl(const uint8_t *left, const uint8_t *right, int pitch, int W, int H,
+                          int D, int ncc_r, int row0, double alpha0, double alpha1, double delta,
+                          const float *inv_l, const float *inv_r, void *vol, int vt, int Wo,
+                          int seg, cudaStream_t st);
+// Segment length of launch_ncc_sl for a W x H frame (a function of the frame
+// size, D, the NCC radius, the volume type and the device only, so that a
+// frame, its bands and a batch pair of that size use the same segments);
+// the environment variable SR_NCC_SEG (1..128) overrides it.
+int ncc_segment(int W, int H, int D, int ncc_r, int vt);
+
 // Overlap of sr_match's kernels by programmatic dependent launch: the two
 // aggregations are launched as programmatic dependents, so each starts
 // while its predecessor drains (once every CTA of the predecessor has

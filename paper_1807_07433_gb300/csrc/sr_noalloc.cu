@@ -163,8 +163,9 @@ extern "C" sr_status sr_match_noalloc(const sr_params *params, double alpha0, do
         return SR_ERR_CUDA;
     if (sr::launch_prep(d_left, d_right, pitch_bytes, Wi, Hi, Di, p.ncc_radius, alpha0, alpha1,
                         delta, 0, rw, mu_l, inv_l, mu_r, inv_r, rowsh, st) != cudaSuccess ||
-        sr::launch_ncc(false, d_left, pitch_bytes, rw, mu_l, inv_l, mu_r, inv_r, Wi, Hi, Di,
-                       p.ncc_radius, volx, p.vol_dtype, st, nullptr, WEi) != cudaSuccess ||
+        sr::launch_ncc_sl(d_left, d_right, pitch_bytes, Wi, Hi, Di, p.ncc_radius, 0, alpha0,
+                          alpha1, delta, inv_l, inv_r, volx, p.vol_dtype, WEi,
+                          sr::ncc_segment(Wi, Hi, Di, p.ncc_radius, p.vol_dtype), st) != cudaSuccess ||
         sr::launch_agg_shear(&tmap, p.vol_dtype, rw, Wi, Hi, Di, p.agg_radius, p.gamma_d,
                              p.gamma_r, lbl_r, nullptr, dbg, st) != cudaSuccess)
         return SR_ERR_CUDA;

@@ -29,7 +29,7 @@ SR_DEBUG_BOUNDS_SELFTEST = 8
 
 # Functions the header declares (tests check the library exports each one).
 EXPORTS = ("sr_create", "sr_destroy", "sr_set_plane", "sr_set_camera", "sr_match",
-           "sr_match_restricted", "sr_match_rows",
+           "sr_match_restricted", "sr_match_rows", "sr_band_rows",
            "sr_match_host", "sr_match_host_async", "sr_match_noalloc", "sr_noalloc_status",
            "sr_bounds_report",
            "sr_match_batch", "sr_set_autotune",
@@ -90,6 +90,7 @@ def load(path: str | None = None):
                 "sr_match_host_async": (i, [vp, vp, vp, vp]),
                 "sr_match_restricted": (i, [vp, vp, vp, i, vp, i, vp, vp]),
                 "sr_match_rows": (i, [vp, vp, vp, i, i, i, vp, vp]),
+                "sr_band_rows": (i, [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
                 "sr_match_noalloc": (i, [ctypes.POINTER(sr_params), d, d, d, vp, vp, i, vp, vp,
                                          vp]),
                 "sr_noalloc_status": (i, [vp]),
@@ -199,6 +200,14 @@ def sr_match_rows(ctx, d_left_rows, d_right_rows, pitch_bytes: int, y0: int, y1:
     _check(ctx, load().sr_match_rows(ctx, _ptr(d_left_rows), _ptr(d_right_rows),
                                      int(pitch_bytes), int(y0), int(y1), _ptr(d_disp_rows),
                                      _ptr(d_wta_rows_or_null)), "sr_match_rows")
+
+
+def sr_band_rows(ctx, y0: int, y1: int) -> tuple[int, int]:
+    """Image rows [r0, r1) that sr_match_rows reads for output rows [y0, y1)."""
+    r0, r1 = ctypes.c_int(0), ctypes.c_int(0)
+    _check(ctx, load().sr_band_rows(ctx, int(y0), int(y1), ctypes.byref(r0), ctypes.byref(r1)),
+           "sr_band_rows")
+    return r0.value, r1.value
 
 
 def sr_match_host(ctx, h_left, h_right, h_disp) -> None:
@@ -433,10 +442,15 @@ class Matcher:
         sr_match_restricted(self.ctx, left, right, pitch, centre, radius, disp, wta)
         return disp
 
+    def band_rows(self, y0, y1):
+        """sr_band_rows: the image rows (r0, r1) that match_rows reads for
+        output rows [y0, y1)."""
+        return sr_band_rows(self.ctx, y0, y1)
+
     def match_rows(self, left_rows, right_rows, y0, y1, disp_rows=None, wta_rows=None):
         """sr_match_rows: rows [y0, y1) of the frame's disparity map from the
-        image rows r0..r1-1 (band plus halo; see bands.plan) given as
-        [r1 - r0, W] CUDA tensors."""
+        image rows r0..r1-1 (band plus halo, band_rows; see bands.plan) given
+        as [r1 - r0, W] CUDA tensors."""
         import torch
         if disp_rows is None:
             disp_rows = torch.empty((y1 - y0, self.W), dtype=torch.float32,

@@ -50,7 +50,7 @@ def run_case(w, vol_dtype):
         if w.D == 64 and H >= 64:
             out["restricted"] = m.match_restricted(dl, dr, 4).cpu().numpy()
             rows = []
-            for b in bands.plan(H, 3, w.ncc_r, w.agg_r):
+            for b in bands.plan(H, 3, w.ncc_r, w.agg_r, read_rows=m.band_rows):
                 rows.append(m.match_rows(dl[b.r0:b.r1].contiguous(), dr[b.r0:b.r1].contiguous(),
                                          b.y0, b.y1).cpu().numpy())
             out["rows"] = np.concatenate(rows)

@@ -17,6 +17,7 @@ import socket
 import sys
 
 import numpy as np
+import pytest
 import torch.multiprocessing as mp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -126,6 +127,14 @@ def test_plan_covers_the_frame_with_halos():
         assert max(b.rows for b in p) - min(b.rows for b in p) <= 1
         for b in p:
             assert b.r0 == max(0, b.y0 - (r + R)) and b.r1 == min(H, b.y1 + r + R)
+    # rows read back to a segment start (the GPU library's rule), and a
+    # read range that misses the halo is refused
+    seg = 32
+    rows = lambda y0, y1: (max(0, max(0, y0 - 5) // seg * seg - 3), min(720, y1 + 8))  # noqa: E731
+    for b in bands.plan(720, 4, 3, 5, read_rows=rows):
+        assert b.r0 <= max(0, b.y0 - 8) and b.r0 % seg in (0, seg - 3) and b.r1 == min(720, b.y1 + 8)
+    with pytest.raises(ValueError):
+        bands.plan(720, 4, 3, 5, read_rows=lambda y0, y1: (y0, y1))
     g = bands.frame_gradient([2.0, 3.0], 10)
     np.testing.assert_array_equal(g, [2.0, 23.0])
     assert bands.band_plane(30.0, 0.08, 100) == (30.0 + 8.0, 0.08)

@@ -1,8 +1,11 @@
 """Row bands of one frame as virtual shards on one GPU: sr_match_rows on
-2, 3 and 4 bands (each from its own rows and halo rows only) gives the
+2, 3 and 4 bands (each from its own rows and halo rows only, as
+sr_band_rows gives them) gives the
 disparity and label maps of one sr_match on the whole frame, bit for bit.
 The bands are planned by paper_1807_07433_gb300.bands, the partition a
 multi-GPU run uses (one band per rank)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -36,7 +39,7 @@ def test_bands_equal_the_whole_frame(w):
         for n in (2, 3, 4):
             got_d = np.full((H, W), -5.0, np.float32)
             got_l = np.full((H, W), -5, np.int16)
-            for b in bands.plan(H, n, w.ncc_r, w.agg_r):
+            for b in bands.plan(H, n, w.ncc_r, w.agg_r, read_rows=m.band_rows):
                 # the band sees only its own rows and halo rows
                 lr = dl[b.r0:b.r1].clone()
                 rr = dr[b.r0:b.r1].clone()
@@ -52,7 +55,8 @@ def test_bands_equal_the_whole_frame(w):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32), want_d.view(np.uint32))
         for y in (0, H - 1):
-            b = [x for x in bands.plan(H, H, w.ncc_r, w.agg_r) if x.y0 == y][0]
+            b = [x for x in bands.plan(H, H, w.ncc_r, w.agg_r, read_rows=m.band_rows)
+                 if x.y0 == y][0]
             d = m.match_rows(dl[b.r0:b.r1].clone(), dr[b.r0:b.r1].clone(), b.y0, b.y1)
             torch.cuda.synchronize()
             np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32),
@@ -69,3 +73,25 @@ def test_band_arguments_are_checked():
             with pytest.raises(sr.SrError) as e:
                 sr.sr_match_rows(m.ctx, buf, buf, 64, y0, y1, out)
             assert e.value.status == sr.SR_ERR_INVALID_ARG
+
+
+def test_band_rows_cover_the_halo_and_start_a_segment():
+    """sr_band_rows: r1 = min(H, y1 + h) and r0 <= y0 - h (or 0); every band's
+    r0 + ncc_r is a multiple of one segment length (or r0 = 0)."""
+    from paper_1807_07433_gb300 import sr
+    W, H, r, R = 1280, 720, 3, 5
+    with sr.Matcher(W, H, 64, r, R, 4.0, 12.0) as m:
+        starts = set()
+        for y0 in range(0, H, 37):
+            y1 = min(H, y0 + 50)
+            r0, r1 = m.band_rows(y0, y1)
+            assert r1 == min(H, y1 + r + R)
+            assert 0 <= r0 <= max(0, y0 - r - R)
+            if r0 > 0:
+                starts.add(r0 + r)
+        g = 0
+        for s0 in starts:
+            g = math.gcd(g, s0)
+        assert g >= 8, sorted(starts)   # segments of at least 8 rows
+        with pytest.raises(sr.SrError):
+            m.band_rows(5, 5)
