@@ -44,12 +44,11 @@
 
 namespace sr {
 
-constexpr int kNslThreads = 128;
 
 template <int RN, int D>
 struct NslCfg {
-    static constexpr int U = 4;                     // columns per thread
-    static constexpr int DB = 8;                    // disparities per thread
+    static constexpr int U = kNslU;                 // columns per thread
+    static constexpr int DB = kNslDB;               // disparities per thread
     static constexpr int NDB = D / DB;              // disparity blocks
     static constexpr int NUG = kNslThreads / NDB;   // column groups
     static constexpr int TX = NUG * U;              // output columns per CTA
@@ -69,7 +68,7 @@ struct NslCfg {
     static constexpr int NC = (CN + kNslThreads - 1) / kNslThreads;        // centres per thread
     static constexpr int NX = (TX + kNslThreads - 1) / kNslThreads;        // columns per thread
     static_assert(D == 16 || D == 32 || D == 64, "D must be 16, 32 or 64");
-    static_assert(U % 4 == 0 && DB % 4 == 0, "padded indices split at multiples of 4");
+    static_assert(U % 4 == 0 && (DB == 4 || DB == 8), "padded indices split at multiples of 4");
 };
 
 template <int RN, int D>
@@ -293,7 +292,7 @@ k_ncc_sl(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, in
             if (u >= Wo) break;
             const float slt = sm.sl[U * ug + k] - n * o;   // block sum of l~
             const float il = sm.il[U * ug + k];
-            float c8[DB];
+            float cst[DB];
 #pragma unroll
             for (int j = 0; j < DB; ++j) {
                 const int cj = D - 1 + k - j;
@@ -303,10 +302,15 @@ k_ncc_sl(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, in
                 const float2 nts = __fmul2_rn(make_float2(-slt, -slt), make_float2(cs.x, cs.y));
                 const float e = fmaf(slt, cs.x, nts.x);
                 const float2 vy = __ffma2_rn(make_float2(n, n), st[k][j], nts);
-                c8[j] = ((vy.x - e) + vy.y) * il * cs.z;
+                cst[j] = ((vy.x - e) + vy.y) * il * cs.z;
             }
             const size_t off = ((size_t)v * Wo + u) * D + d0;
-            if (SR_CHECK(off + DB - 1, (long long)H * Wo * D, 113)) store8(vol + off, c8);
+            if (SR_CHECK(off + DB - 1, (long long)H * Wo * D, 113)) {
+                if constexpr (DB == 8)
+                    store8(vol + off, cst);
+                else
+                    store4(vol + off, cst);
+            }
         }
     };
 

@@ -291,7 +291,7 @@ int ncc_segment(int W, int H, int D, int ncc_r, int vt) {
         sms = 1;
     (void)vt;
     const int occ = kNslResident;   // a constant, so that every build picks the same segments
-    const int tx = 4096 / D;
+    const int tx = kNslThreads / (D / kNslDB) * kNslU;   // columns of a CTA
     const long long nx = (W + D - 1 + tx - 1) / tx;
     const int hi = std::min(std::max(H, 1), kNslMaxSeg), lo = std::min(hi, 8);
     int best = hi;

@@ -104,6 +104,19 @@ __device__ __forceinline__ void store8(__nv_bfloat16 *p, const float *v) {
     *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(h);
 }
 
+// Stores of four costs: one 16-byte (FP32) or 8-byte (16-bit) store.
+__device__ __forceinline__ void store4(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(__half *p, const float *v) {
+    __half2 h[2] = {__floats2half2_rn(v[0], v[1]), __floats2half2_rn(v[2], v[3])};
+    *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16 *p, const float *v) {
+    __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v[0], v[1]), __floats2bfloat162_rn(v[2], v[3])};
+    *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
+}
+
 // Sec. II-A row shift of image row v, s(v) = alpha0 + alpha1 v - delta: the
 // plane of Eq. 2, evaluated once per image row in FP64 (a row's shift enters
 // the warp as its integer part and fraction, and the post-processing of Sec.
@@ -166,6 +179,8 @@ cudaError_t launch_ncc(bool target, const uint8_t *left, int pitch, const float 
 
 constexpr int kNslMaxSeg = 128;   // longest row segment of launch_ncc_sl
 constexpr int kNslResident = 3;   // its CTAs per SM (launch bound)
+constexpr int kNslThreads = 128;  // its threads per CTA
+constexpr int kNslU = 4, kNslDB = 8;   // columns and disparities per thread
 
 // Eq. 3 reference volume [H][Wo][D] (Wo = W or the extended W + D - 1)
 // from exact integer window sums (k_ncc_sl.cuh): the left and right images
