@@ -487,7 +487,10 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
             // column and serves PX pixels x the valid output rows
             const VT *rs = SH ? ring + (j & 1) * C::RINGS + bx * C::CW
                               : ring + (j & 1) * C::RINGS + bx * C::CS;
-            auto body = [&](auto all_rows) {
+            // output rows lo..hi (compile-time) use source row j: row py
+            // takes tap row j - py, valid for j - WS < py <= j
+            auto body = [&](auto lo_c, auto hi_c) {
+                constexpr int LO = decltype(lo_c)::value, HI = decltype(hi_c)::value;
                 float2 cst[PX + 2 * R][DL / 2];
                 auto load_col = [&](int i) {
                     if constexpr (SH) {
@@ -531,7 +534,7 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
                     load_col(dx + PX - 1);
 #pragma unroll
                     for (int py = 0; py < kAggTY; ++py) {
-                        if (decltype(all_rows)::value || (unsigned)(j - py) < (unsigned)C::WS) {
+                        if (py >= LO && py <= HI) {
                             // the weights of the lane's pixels, each paired
                             // with itself for the paired multiply-add
                             float2 w[PX];
@@ -560,10 +563,18 @@ __device__ __forceinline__ void agg_tile(const AggSmem<R, D, VT, SH, BAND> &sm, 
                     }
                 }
             };
-            if (j >= kAggTY - 1 && j < C::WS)
-                body(std::integral_constant<bool, true>());   // all output rows use row j
-            else
-                body(std::integral_constant<bool, false>());
+            // the rows that use source row j: 0..min(3, j) for the first
+            // rows, lo..3 with lo = j - WS + 1 for the last; all four between
+            const int lo = max(0, j - C::WS + 1), hi = min(kAggTY - 1, j);
+            using std::integral_constant;
+            if (lo == 0 && hi == 3) body(integral_constant<int, 0>(), integral_constant<int, 3>());
+            else if (lo == 0 && hi == 0) body(integral_constant<int, 0>(), integral_constant<int, 0>());
+            else if (lo == 0 && hi == 1) body(integral_constant<int, 0>(), integral_constant<int, 1>());
+            else if (lo == 0 && hi == 2) body(integral_constant<int, 0>(), integral_constant<int, 2>());
+            else if (lo == 1 && hi == 3) body(integral_constant<int, 1>(), integral_constant<int, 3>());
+            else if (lo == 2 && hi == 3) body(integral_constant<int, 2>(), integral_constant<int, 3>());
+            else if (lo == 3 && hi == 3) body(integral_constant<int, 3>(), integral_constant<int, 3>());
+            else if (lo == 1 && hi == 2) body(integral_constant<int, 1>(), integral_constant<int, 2>());
         }
         ph ^= 1u << (j & 1);   // every source row completes one phase of its slot
         __syncthreads();
