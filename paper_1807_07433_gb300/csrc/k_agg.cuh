@@ -211,19 +211,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, 
 }
 // Wait for the phase of the given parity; gives up after max_cycles SM clocks
 // (then records the timeout in *err and returns false).
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
                                           long long max_cycles, int *err) {
     const unsigned a = smem_addr(bar);
+    if (mbar_try(a, parity)) return true;   // usually complete: no clock read
     const long long t0 = clock64();
     while (true) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(a, parity)) return true;
         if (clock64() - t0 > max_cycles) {
             if (err) atomicExch(err, 1);
             return false;
