@@ -242,15 +242,19 @@ dim3 grid_for(int w, int h) { return dim3((w + kBX - 1) / kBX, (h + kBY - 1) / k
 // block's rows for every staged column, then each centre sums 2 RN + 1 of
 // them -- in exact integers, so they equal stats_left_px's.  Warped-target
 // statistics: the centred two-pass form of stats_right_px, in its order (a
-// running sum of squares would cancel in FP32 on smooth blocks).
+// running sum of squares would cancel in FP32 on smooth blocks).  A thread
+// computes two vertically adjacent centres, whose blocks share 2 RN rows:
+// their 2 RN + 2 rows of values are read from shared memory once, into
+// registers, and the row sums of (value - 128) serve both means.
 template <int RN>
-__global__ void __launch_bounds__(kBX * kBY)
+__global__ void __launch_bounds__(kBX * kBY / 2)
 k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int pitch, int W,
        int H, int D, double alpha0, double alpha1, double delta, int row0,
        float *__restrict__ rw, float *__restrict__ mu_l, float *__restrict__ inv_l,
        float *__restrict__ mu_r, float *__restrict__ inv_r, float2 *__restrict__ rowsh) {
     constexpr int B = 2 * RN + 1, TH = kBY + 2 * RN, TW = kBX + 2 * RN;
     constexpr int n = B * B;
+    constexpr int NT = kBX * kBY / 2;     // threads: each computes two rows of the tile
     __shared__ int s_l[TH][TW];           // left intensities
     __shared__ float s_r[TH][TW];         // warped target intensities
     __shared__ unsigned s_cs[kBY][TW];    // left column sums over the block rows
@@ -274,12 +278,12 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
     }
     __syncthreads();
     {   // all loads of a thread first, then the stores: their latencies overlap
-        constexpr int NI = (TH * TW + kBX * kBY - 1) / (kBX * kBY);
+        constexpr int NI = (TH * TW + NT - 1) / NT;
         int lv[NI];
         float av[NI], bv[NI];
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
-            const int i = min(tid + k * kBX * kBY, TH * TW - 1);
+            const int i = min(tid + k * NT, TH * TW - 1);
             const int r = i / TW, c = i % TW;
             const int y = clampi(y0 - RN + r, 0, H - 1);
             const int xl = clampi(x0 - RN + c, 0, W - 1);
@@ -294,7 +298,7 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
         }
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
-            const int i = tid + k * kBX * kBY;
+            const int i = tid + k * NT;
             if (i < TH * TW) {
                 const int r = i / TW, c = i % TW;
                 s_l[r][c] = lv[k];
@@ -303,7 +307,7 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
         }
     }
     __syncthreads();
-    for (int i = tid; i < kBY * TW; i += kBX * kBY) {   // column sums of B rows
+    for (int i = tid; i < kBY * TW; i += NT) {   // column sums of B rows
         const int r = i / TW, c = i % TW;
         unsigned cs = 0, cs2 = 0;
 #pragma unroll
@@ -316,49 +320,66 @@ k_prep(const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, int 
         s_cs2[r][c] = cs2;
     }
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int xi = x0 + tx, v = y0 + ty;
-    if (xi >= WE || v >= H) return;
-    if (!SR_CHECK((size_t)v * WE + xi, (long long)H * WE, 305)) return;
-    // left block at centre xi (exact integer sums)
-    {
-        unsigned su = 0, s2 = 0;
+    // this thread: tile rows ty and ty + 1 of column tx; their warped blocks
+    // share B - 1 rows, so the B + 1 rows of values are read once into
+    // registers.  Each pixel's arithmetic is the order of stats_right_px.
+    const int tx = threadIdx.x, ty = 2 * threadIdx.y;
+    const int xi = x0 + tx;
+    if (xi >= WE) return;
+    float vv[B + 1][B];
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            su += s_cs[ty][tx + i];
-            s2 += s_cs2[ty][tx + i];
-        }
-        const long long q = (long long)n * s2 - (long long)su * su;   // n^2 var, exact
-        const float var = (float)q / (float)(n * n);
-        inv_l[(size_t)v * WE + xi] = (var < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)q);
-        mu_l[(size_t)v * WE + xi] = (float)su / (float)n;
+    for (int j = 0; j < B + 1; ++j)
+#pragma unroll
+        for (int i = 0; i < B; ++i) vv[j][i] = s_r[ty + j][tx + i];
+    // row sums of (value - 128), shared by the two blocks
+    float rsum[B + 1];
+#pragma unroll
+    for (int j = 0; j < B + 1; ++j) {
+        float rs = 0.0f;
+#pragma unroll
+        for (int i = 0; i < B; ++i) rs += vv[j][i] - kNccOffset;
+        rsum[j] = rs;
     }
-    // warped-target block at centre xi - (D-1): mean from row sums of
-    // (value - 128), then centred squares
-    {
-        float s = 0.0f;
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            float rs = 0.0f;
-#pragma unroll
-            for (int i = 0; i < B; ++i) rs += s_r[ty + j][tx + i] - kNccOffset;
-            s += rs;
-        }
-        const float m = kNccOffset + s / (float)n;
-        float q = 0.0f;
-#pragma unroll
-        for (int j = 0; j < B; ++j)
+    for (int h = 0; h < 2; ++h) {
+        const int r = ty + h, v = y0 + r;
+        if (v >= H) break;
+        if (!SR_CHECK((size_t)v * WE + xi, (long long)H * WE, 305)) break;
+        // left block at centre xi (exact integer sums)
+        {
+            unsigned su = 0, s2 = 0;
 #pragma unroll
             for (int i = 0; i < B; ++i) {
-                const float c = s_r[ty + j][tx + i] - m;
-                q = fmaf(c, c, q);
+                su += s_cs[r][tx + i];
+                s2 += s_cs2[r][tx + i];
             }
-        inv_r[(size_t)v * WE + xi] = (q / (float)n < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)n * q);
-        mu_r[(size_t)v * WE + xi] = m;
+            const long long q = (long long)n * s2 - (long long)su * su;   // n^2 var, exact
+            const float var = (float)q / (float)(n * n);
+            inv_l[(size_t)v * WE + xi] = (var < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)q);
+            mu_l[(size_t)v * WE + xi] = (float)su / (float)n;
+        }
+        // warped-target block at centre xi - (D-1): mean from row sums of
+        // (value - 128), then centred squares
+        {
+            float s = 0.0f;
+#pragma unroll
+            for (int j = 0; j < B; ++j) s += rsum[h + j];
+            const float m = kNccOffset + s / (float)n;
+            float q = 0.0f;
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+#pragma unroll
+                for (int i = 0; i < B; ++i) {
+                    const float c = vv[h + j][i] - m;
+                    q = fmaf(c, c, q);
+                }
+            inv_r[(size_t)v * WE + xi] = (q / (float)n < kFlatVar) ? 0.0f : 1.0f / sqrtf((float)n * q);
+            mu_r[(size_t)v * WE + xi] = m;
+        }
+        // the warped image, at the target columns this tile owns
+        const int xr = xi - (D - 1);
+        if (xr >= 0 && SR_CHECK(xr, W, 306)) rw[(size_t)v * W + xr] = vv[h + RN][RN];
     }
-    // the warped image, at the target columns this tile owns
-    const int xr = xi - (D - 1);
-    if (xr >= 0 && SR_CHECK(xr, W, 306)) rw[(size_t)v * W + xr] = s_r[ty + RN][tx + RN];
 }
 
 }  // namespace
@@ -367,7 +388,7 @@ cudaError_t launch_prep(const uint8_t *left, const uint8_t *right, int pitch, in
                         int ncc_r, double alpha0, double alpha1, double delta, int row0,
                         float *rw, float *mu_l, float *inv_l, float *mu_r, float *inv_r,
                         float2 *rowsh, cudaStream_t st) {
-    const dim3 grid = grid_for(W + D - 1, H), block(kBX, kBY);
+    const dim3 grid = grid_for(W + D - 1, H), block(kBX, kBY / 2);
     switch (ncc_r) {
 #define SR_PREP(RN_)                                                                          \
     case RN_:                                                                                 \
