@@ -123,7 +123,11 @@ sr_status sr_set_camera(sr_ctx *ctx, double f_px, double baseline, double u0, do
  *                    disparity l_ref of the reference view.
  * The NCC cost (Eq. 3) is computed once, as the reference volume over
  * W + D - 1 columns; the target view of Sec. II-B-1 reads it at column
- * u + d.  Four kernels: prep, ncc, agg_tgt, agg_ref; the last one also
+ * u + d.  Its numerator is split into an exact integer part and the part
+ * the row shifts' fractions carry (only the latter is rounded), with window
+ * sums kept per segment of image rows, so the costs' last bits depend on
+ * the segment length, a function of the frame size (SR_NCC_SEG overrides
+ * it).  Four kernels: prep, ncc, agg_tgt, agg_ref; the last one also
  * runs the L-R check and the post-processing on its WTA labels.  The first
  * call builds the tensor map of that read.  Asynchronous on the context's
  * stream.  Errors: SR_ERR_INVALID_ARG for null images/output or pitch < W,
@@ -153,8 +157,8 @@ sr_status sr_match(sr_ctx *ctx, const uint8_t *d_left, const uint8_t *d_right, i
  *   d_wta_rows_or_null         optional (y1 - y0) x W int16: the same rows
  *                              of sr_match's d_wta_or_null
  * The halo rows are matched too (and discarded), so a band costs its rows
- * plus up to 2h rows and one NCC row segment (sr_band_rows).  Uses the context's scratch (sr_get_buffer reports
- * SR_ERR_STATE afterwards); the first call allocates 6*W*H bytes of band
+ * plus up to 2h rows and one NCC row segment (sr_band_rows).  Uses the
+ * context's scratch (sr_get_buffer reports SR_ERR_STATE afterwards); the first call allocates 6*W*H bytes of band
  * output and builds a tensor map for bands of r1 - r0 rows (rebuilt when
  * that count changes).  Asynchronous.  Errors: SR_ERR_INVALID_ARG,
  * SR_ERR_OOM, SR_ERR_CUDA. */

@@ -44,7 +44,6 @@
 
 namespace sr {
 
-
 template <int RN, int D>
 struct NslCfg {
     static constexpr int U = kNslU;                 // columns per thread
